@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the Wilson-clover QCD+QED Dirac operator and its solvers on one
+GB300 (or N replicas under torchrun).
+
+Workload (one step): solve D psi = eta to a true FP64 relative residual of 1e-10
+on the 32^3 x 64 lattice with C* boundary conditions in the three spatial
+directions (simulated extended lattice 64 x 64 x 32 x 32, V = 4,194,304 sites),
+antiperiodic time, stout-smeared synthetic SU(3) links (5 steps, rho = 0.1) and
+Gaussian U(1) angles, flavour qhat = 4, kappa = 0.137312, csw = 1.90952 / 1.0,
+with the mixed-precision solver (flexible GCR on Dhat in FP32 inside FP64
+defect correction).
+
+Reported:
+  value      operator throughput inside the timed solves in Gflop/s: every
+             half-lattice hopping launch counts 2112 flop per output site (so one
+             D_w or one Dhat application = 2112 V flop), divided by the device time;
+  time_to_solution   the same solve (ms_per_step) against the plain FP64 CGNE solve;
+  roofline   the dominant kernel's algorithmic bytes per launch / its mean
+             CUDA-event duration, against the measured HBM copy bandwidth;
+  e2e        the same metric through the C ABI with pinned HOST buffers (the
+             library copies eta in and psi out inside the timed call);
+  cpu_baseline  the FP64 oracle applying D_w to a bounded sample of sites.
+
+--impl reference times the oracle (the plain CPU implementation) on the same
+metric, each step a bounded sample of sites of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Dw Gflop/s & % HBM roofline; time-to-1e-10 residual vs plain FP64 GPU solve"
+FLOP_PER_SITE = 2112
+
+WORKLOADS = {
+    "32^3x64-cstar3": dict(L=(64, 32, 32, 32), cstar=3, theta=(math.pi, 0.0, 0.0, 0.0), qhat=4,
+                           kappa=0.137312, su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=2000,
+                           src_seed=2001, stout=5, rho=0.1),
+    # small case for profiler captures and quick checks (8^4, antiperiodic time)
+    "8^4": dict(L=(8, 8, 8, 8), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,
+                su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=1000, src_seed=1001, stout=0, rho=0.1),
+    "16^4": dict(L=(16, 16, 16, 16), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,
+                 su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=4000, src_seed=4001, stout=5, rho=0.1),
+}
+
+
+def workload_desc(name, w):
+    L = w["L"]
+    ext = (L[0], 2 * L[1] if w["cstar"] else L[1], L[2], L[3])
+    return {
+        "workload": f"{name}: Wilson-clover SU(3)xU(1) Dirac solve to 1e-10, physical {L[3]}x{L[2]}x{L[1]}x{L[0]}"
+                    f" (x,y,z,t), C* dirs={w['cstar']}, simulated {'x'.join(map(str, ext))}",
+        "V": int(np.prod(ext)),
+        "qhat": w["qhat"], "kappa": w["kappa"], "su3csw": w["su3csw"], "u1csw": w["u1csw"],
+        "stout_steps": w["stout"], "rho": w["rho"], "field_seed": w["field_seed"], "source_seed": w["src_seed"],
+        "solver": "FGCR(nkv=16) on Dhat, FP32 inner, FP64 defect correction",
+        "tol": 1e-10,
+        "l2": "working set (links, SW terms, Krylov vectors) >> 129 MB L2; no flush",
+    }
+
+
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------------
+def oracle_rate(w, U, A, psi, seconds, rng_seed=0):
+    """FP64 oracle applying D_w at a random sample of sites; returns (Gflop/s, sites, s)."""
+    from oracle import DiracOperator, Flavour, GaugeField, Geometry
+    geom = Geometry(w["L"], w["cstar"], w["theta"])
+    op = DiracOperator(GaugeField(geom, U, A, w["invqel"]),
+                       Flavour(w["qhat"], w["kappa"], w["su3csw"], w["u1csw"]))
+    rng = np.random.default_rng(rng_seed)
+    n = 512
+    t0 = time.perf_counter()
+    op.apply(psi, rng.choice(geom.V, n, replace=False))
+    dt = time.perf_counter() - t0
+    n = int(min(geom.V // 8 - 1, max(512, n * seconds / max(dt, 1e-3))))
+    sites = rng.choice(geom.V, n, replace=False)
+    t0 = time.perf_counter()
+    op.apply(psi, sites)
+    dt = time.perf_counter() - t0
+    return FLOP_PER_SITE * n / dt / 1e9, n, dt
+
+
+def make_inputs(w, device):
+    from paper_1908_11673_gb300 import workload
+    U, A = workload.gauge_field(w["L"], w["field_seed"], stout_steps=w["stout"], rho=w["rho"], device=device)
+    V = int(np.prod(w["L"])) * (2 if w["cstar"] else 1)
+    eta = workload.spinor(V, w["src_seed"])
+    return U, A, eta
+
+
+# ----------------------------------------------------------------------------------
+def run_reference(args, w, name):
+    """The oracle on the host cores: each step a bounded sample of sites."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    U, A, eta = make_inputs(w, "cpu")
+    seconds = float(os.environ.get("QXD_REF_STEP_SECONDS", "5"))
+    for i in range(args.warmup):
+        oracle_rate(w, U, A, eta, min(seconds, 1.0), rng_seed=100 + i)
+    flops, secs, nsites = 0.0, 0.0, 0
+    for i in range(args.steps):
+        rate, n, dt = oracle_rate(w, U, A, eta, seconds, rng_seed=i)
+        flops += rate * dt * 1e9
+        secs += dt
+        nsites += n
+    value = flops / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(name, w),
+        "cpu_baseline": {"value": value, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
+                         "sample": f"D_w at {nsites} random sites of the workload over {args.steps} steps "
+                                   f"(NumPy FP64, one process)"},
+        "e2e": {"value": value, "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args, w, name):
+    import torch
+
+    from paper_1908_11673_gb300 import build, qxd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    U, A, eta = make_inputs(w, f"cuda:{local}")
+    ctx = qxd.Context(w["L"], w["cstar"], w["theta"], device=local)
+    t0 = time.perf_counter()
+    ctx.set_links(U, A, w["invqel"], stream=stream)
+    ctx.set_clover(0, w["qhat"], w["kappa"], w["su3csw"], w["u1csw"], stream=stream)
+    setup_s = time.perf_counter() - t0
+    V = ctx.V
+    eta_d = torch.from_numpy(eta).to(dev)
+    psi_d = torch.empty_like(eta_d)
+    solve_kw = dict(kind=qxd.FGCR, tol=1e-10, inner=qxd.FP32, nkv=16, nmx=100000, stream=stream)
+
+    for _ in range(args.warmup):
+        ctx.solve(0, eta_d, psi_d, **solve_kw)
+    torch.cuda.synchronize()
+
+    def timed(fn, k):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [fn() for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    # ---- timed region: K mixed-precision solves, kernels timed by event pairs -----
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile(2)
+    ms, infos = timed(lambda: ctx.solve(0, eta_d, psi_d, **solve_kw), args.steps)
+    prof = ctx.profile_entries()
+    ctx.profile(0)
+    clocks = sampler.stop()
+    hops = [p for p in prof if p["name"].startswith("hop_")]
+    hop_launches = sum(p["launches"] for p in hops)
+    flops = hop_launches * (V // 2) * FLOP_PER_SITE
+    launches = sum(p["launches"] for p in prof)
+    total_ms_k = sum(p["ms"] for p in prof)
+    value_rank = flops / (ms * 1e-3) / 1e9
+
+    # ---- e2e: pinned host buffers through the C ABI ----------------------------------
+    eta_h = torch.from_numpy(eta).pin_memory()
+    psi_h = torch.empty_like(eta_h).pin_memory()
+    ms_e2e, infos_e2e = timed(lambda: ctx.solve(0, eta_h, psi_h, **solve_kw), max(1, min(args.steps, 3)))
+    k_e2e = max(1, min(args.steps, 3))
+    e2e_value = flops / args.steps * k_e2e / (ms_e2e * 1e-3) / 1e9
+
+    # ---- plain FP64 CGNE on the same system ---------------------------------------------
+    base = None
+    if not args.no_fp64_baseline:
+        ms64, inf64 = timed(lambda: ctx.solve(0, eta_d, psi_d, kind=qxd.CGNE, tol=1e-10, nmx=200000,
+                                              stream=stream), 1)
+        base = {"fp64_cgne_ms": ms64, "iters": inf64[0].iters, "true_relres": inf64[0].true_relres}
+
+    # ---- aggregate over ranks ----------------------------------------------------------
+    total_value = value_rank
+    if dist:
+        t = torch.tensor([flops], device=dev, dtype=torch.float64)
+        dist.all_reduce(t)
+        total_value = float(t.item()) / (ms * 1e-3) / 1e9
+    if rank != 0:
+        ctx.close()
+        dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = measured_peaks()
+    dom = max(prof, key=lambda p: p["ms"])
+    mean_ms = dom["ms"] / dom["launches"]
+    bytes_per_launch = dom["bytes"] / dom["launches"]
+    achieved = bytes_per_launch / (mean_ms * 1e-3) / 1e9
+    kernels = []
+    for p in sorted(prof, key=lambda p: -p["ms"]):
+        gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None
+        kernels.append({"name": p["name"], "launches": p["launches"], "ms": round(p["ms"], 3),
+                        "share": round(p["ms"] / total_ms_k, 4) if total_ms_k else None,
+                        "GB/s": round(gbs, 1) if gbs else None})
+    info = infos[-1]
+    tts = {"mixed_ms": ms / args.steps, "iters_inner": info.iters, "outer_restarts": info.restarts,
+           "true_relres": info.true_relres}
+    if base:
+        tts.update(base)
+        tts["speedup_vs_fp64_cgne"] = base["fp64_cgne_ms"] / (ms / args.steps)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        Uh, Ah = U, A
+        rate, n, dt = oracle_rate(w, Uh, Ah, eta, float(os.environ.get("QXD_CPU_SECONDS", "15")))
+        cpu = {"value": rate, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
+               "sample": f"D_w at {n} random sites of the workload ({dt:.1f} s, NumPy FP64, one process)"}
+
+    line = {
+        "metric": METRIC, "value": total_value, "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": workload_desc(name, w) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "time_to_solution": tts,
+        "roofline": {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs copy)",
+                     "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_ms, "traffic": None},
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "Gflop/s", "h2d_bytes_per_step": int(eta.nbytes),
+                "d2h_bytes_per_step": int(eta.nbytes), "ms_per_step": ms_e2e / k_e2e},
+        "gpu_launches": launches,
+        "setup_s": setup_s,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="32^3x64-cstar3")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, args.workload)
+    return run_native(args, w, args.workload)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,211 @@
+/*
+ * qxd.h - C ABI of libqxd: the O(a)-improved Wilson-Dirac operator with
+ * combined SU(3) x U(1) links, SU(3) and U(1) Sheikholeslami-Wohlert terms,
+ * even-odd preconditioning, phase-periodic and C* boundary conditions, and
+ * the solvers built on it, on one NVIDIA GB300 (sm_103a).
+ *
+ * Definitions follow openQ*D (Campos et al., arXiv:1908.11673):
+ *   operator           Sec. 2.2, eqs. dirac, wilson-dirac, frw-covder, bkw-covder
+ *   SW term            Sec. 2.2, eq. sw-term and the U(1) field tensor below it
+ *   even-odd operator  Sec. 2.2, definition of D-hat
+ *   C* boundaries      Sec. 2.1, eqs. cstar-bc, ext-periodic-bc, ext-shifted-bc
+ *   solvers            Sec. 4.4 (CG, MSCG, GCR); shifts of App. A.1/A.2
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice.  mu = 0 is time.  The physical lattice is L0 x L1 x L2 x L3.  With
+ *   C* in `cstar` >= 1 directions (turned on in the order 1, 2, 3) the simulated
+ *   lattice is the extended lattice L0 x 2L1 x L2 x L3; otherwise it is the
+ *   physical one.  V = number of simulated sites, V_e = V_o = V/2.
+ * Site order.  Lexicographic over the simulated lattice, x0 slowest:
+ *   idx = ((x0*N1 + x1)*N2 + x2)*N3 + x3  (N = simulated extents).
+ *   Parity = (x0+x1+x2+x3) mod 2, 0 = even.  Because N3 is even, an even-site
+ *   (odd-site) vector lists the even (odd) sites in lexicographic order, and
+ *   site idx sits at position idx/2.
+ * Spinors.  [site][spin 4][colour 3] complex, interleaved (re, im).  FP64 entry
+ *   points take complex128 (double pairs), FP32 ones complex64 (float pairs).
+ *   Several right-hand sides are stored one after the other: [nrhs][V or V/2][4][3].
+ * Gamma matrices.  Chiral basis: gamma_0 = [[0,-1],[-1,0]],
+ *   gamma_k = [[0,-i s_k],[i s_k,0]] (s_k Pauli matrices), gamma_5 = diag(1,1,-1,-1);
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu].
+ * Pointers.  Every array argument may be host memory or device memory of the
+ *   context's GPU; the library looks at each pointer (cudaPointerGetAttributes)
+ *   and stages host arrays through its own device buffers.  The caller owns all
+ *   arrays it passes; the library owns its internal copies of links, SW terms
+ *   and workspace and frees them in qxd_destroy.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Operator
+ *   applications on device arrays are asynchronous on that stream; calls that
+ *   take or return host arrays, and all solves, synchronise it before returning.
+ * Errors.  Every call returns a qxd_status; 0 is success.  No C++ exception
+ *   crosses the ABI.  qxd_last_error() gives a message for the last failure on
+ *   a context.  Arguments are checked before any launch.
+ */
+#ifndef QXD_H
+#define QXD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QXD_OK = 0,
+    QXD_EARG = 1,        /* invalid argument (geometry, sizes, flavour id, precision) */
+    QXD_ENOCONV = 2,     /* solver reached nmx without meeting its tolerance */
+    QXD_EBREAKDOWN = 3,  /* Krylov breakdown (zero denominator) */
+    QXD_ENAN = 4,        /* non-finite value in a source or during a solve */
+    QXD_ECUDA = 5,       /* CUDA runtime error */
+    QXD_ENOMEM = 6,      /* device allocation failed */
+    QXD_ESTATE = 7       /* call out of order (e.g. operator before set_links/set_clover) */
+} qxd_status;
+
+typedef enum { QXD_FP64 = 0, QXD_FP32 = 1, QXD_BF16 = 2 } qxd_prec;
+
+typedef enum { QXD_CGNE = 0, QXD_FGCR = 1, QXD_MSCG = 2 } qxd_solver_kind;
+
+typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1 } qxd_precond_kind;
+
+/* Geometry (Sec. 2.1).  Every L[mu] must be even and >= 2.
+ * cstar in 0..3: C* boundary conditions in directions 1..cstar.
+ * theta[mu]: fermion phase psi(x + L_mu e_mu) = exp(i theta_mu) psi(x)
+ * (eq. periodic-bc-quark); theta[0] = pi gives antiperiodic time.  With
+ * cstar > 0 the spatial phases theta[1..3] must be 0 (Sec. 2.1). */
+typedef struct {
+    int L[4];
+    int cstar;
+    double theta[4];
+} qxd_geom;
+
+/* One quark flavour (input-file section [Flavour n], App. C):
+ * qhat = q/qel (integer charge), kappa (a m0 = 1/(2 kappa) - 4),
+ * su3csw, u1csw = SW coefficients of eq. sw-term. */
+typedef struct {
+    int qhat;
+    double kappa;
+    double su3csw;
+    double u1csw;
+} qxd_flavour;
+
+/* Solver parameters.
+ * kind   : QXD_CGNE  - CG on Dhat^+ Dhat in FP64 (the plain FP64 solver);
+ *          QXD_FGCR  - flexible GCR on Dhat in precision `inner`, restarted every
+ *                      nkv steps, inside FP64 defect correction;
+ *          QXD_MSCG  - multi-shift CG (only with qxd_solve_multishift).
+ * tol    : target true relative residual |eta - D psi| / |eta| (FP64, full lattice)
+ *          for qxd_solve, |phi - (Dhat^+Dhat + s_j) x_j| / |phi| for each shift j.
+ * nmx    : maximum number of operator applications of the Krylov solver
+ *          (for defect correction: summed over the inner solves).
+ * nkv    : GCR restart length (1..64).
+ * inner  : precision of the inner Krylov solver (QXD_FP32 or QXD_BF16 storage;
+ *          QXD_FP64 makes FGCR a plain FP64 solver).
+ * inner_tol : relative residual reduction requested from each inner solve
+ *          (0 selects 1e-5 for FP32 and 5e-3 for BF16 storage).
+ * precond: right preconditioner of FGCR (QXD_PRECOND_NONE or QXD_PRECOND_LEARNED). */
+typedef struct {
+    int kind;
+    double tol;
+    int nmx;
+    int nkv;
+    int inner;
+    double inner_tol;
+    int precond;
+} qxd_solver;
+
+/* Solver report.  true_relres is always recomputed in FP64 from the returned
+ * solution.  op_applies counts applications of Dhat (or D) in any precision. */
+typedef struct {
+    int status;
+    int iters;
+    int restarts;
+    int op_applies;
+    double true_relres;
+} qxd_info;
+
+typedef struct qxd_ctx qxd_ctx;
+
+/* Create a context on CUDA device `device` for geometry `g`.
+ * Errors: QXD_EARG for an odd or non-positive extent, cstar outside 0..3, or a
+ * non-zero spatial theta with cstar > 0; QXD_ECUDA if the device is unusable. */
+int qxd_create(const qxd_geom* g, int device, qxd_ctx** out);
+
+/* Free every device buffer of the context.  NULL is allowed. */
+void qxd_destroy(qxd_ctx* ctx);
+
+/* Load the gauge field given on the PHYSICAL lattice (Sec. 2):
+ *   U: complex128 [Vphys][4][3][3] SU(3) links U_mu(x) (row-major colour matrix),
+ *   A: float64   [Vphys][4] photon field A_mu(x), z_mu(x) = exp(i A_mu(x)).
+ * With C* the mirror half is filled by the library from the orbifold
+ * constraint U(x + L1 e1) = U(x)^*, A(x + L1 e1) = -A(x) (eq. cstar-bc-gauge).
+ * invqel = 1/qel (elementary charge) is kept for reference; the operator does not
+ * depend on it (q Ahat = qhat (i/4) Im sum z_{mu nu}).
+ * Invalidates every SW term set before.  Synchronises `stream`. */
+int qxd_set_links(qxd_ctx* ctx, const double* U, const double* A, double invqel, void* stream);
+
+/* Build, for flavour slot fl (0..7), the hopping phases z^qhat (with the
+ * boundary phases folded in), the site-diagonal term 1/(2 kappa) + dD_sw
+ * (eq. sw-term; two Hermitian 6x6 chiral blocks per site) and its inverse on
+ * every site, in FP64 with FP32 and BF16 copies.
+ * Errors: QXD_ESTATE before qxd_set_links; QXD_EARG for fl outside 0..7 or
+ * kappa <= 0; QXD_ENAN if a diagonal block is singular.  Synchronises `stream`. */
+int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream);
+
+/* out = D in on the full simulated lattice (eq. dirac with dD_b = 0), for nrhs
+ * right-hand sides.  in, out: [nrhs][V][4][3] complex128 (prec = QXD_FP64) or
+ * complex64 (QXD_FP32, and QXD_BF16 which stores spinors in bfloat16 inside the
+ * kernel and accumulates in FP32).  in and out must not overlap. */
+int qxd_apply_Dw(qxd_ctx* ctx, int fl, int prec, const void* in, void* out, int nrhs, void* stream);
+
+/* out_e = Dhat in_e = (D_ee - D_eo D_oo^-1 D_oe) in_e (Sec. 2.2) on even-site
+ * vectors [nrhs][V/2][4][3].  If dagger != 0 applies Dhat^+ = gamma5 Dhat gamma5. */
+int qxd_apply_Dhat_eo(qxd_ctx* ctx, int fl, int prec, int dagger, const void* in_e, void* out_e,
+                      int nrhs, void* stream);
+
+/* Solve D psi = eta on the full lattice (complex128 [nrhs][V][4][3]) to the true
+ * relative residual s->tol.  CGNE: even-odd system, CG on Dhat^+ Dhat in FP64,
+ * odd sites reconstructed.  FGCR: FP64 defect correction whose inner solves run
+ * flexible GCR on Dhat in precision s->inner.  info (may be NULL) receives the
+ * report of the last right-hand side (status is the worst over all of them).
+ * Returns QXD_ENOCONV if any right-hand side misses the tolerance within nmx. */
+int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* psi, int nrhs,
+              qxd_info* info, void* stream);
+
+/* Multi-shift CG (Sec. 4.4 MSCG; App. A.2): x_j = (Dhat^+ Dhat + sigma[j])^-1 phi_e
+ * for j = 0..nshift-1 (1 <= nshift <= 32, sigma[j] >= 0), phi_e and each x_j
+ * complex128 [V/2][4][3]; x_e holds the nshift solutions one after the other.
+ * s->inner = QXD_FP64 runs the Krylov space in FP64; QXD_FP32 runs it with the
+ * FP32 operator and then refines each shift by FP64 defect correction. */
+int qxd_solve_multishift(qxd_ctx* ctx, int fl, int nshift, const double* sigma, const qxd_solver* s,
+                         const void* phi_e, void* x_e, qxd_info* info, void* stream);
+
+/* Learned preconditioner weights for flavour fl (used by FGCR with
+ * QXD_PRECOND_LEARNED).  The network M has nlayers gauge-covariant layers
+ *   psi'_c(x) = sum_{c'} sum_{d=0..8} W[l][c][c'][d] T_d psi_{c'}(x),
+ * T_0 = 1, T_{1+mu} psi(x) = V_mu(x) psi(x+mu), T_{5+mu} psi(x) = V_mu(x-mu)^+ psi(x-mu),
+ * with V = U z^qhat and the boundary conditions of D; channel counts
+ * 1 -> nch -> ... -> nch -> 1.  W: float32 complex, per layer
+ * [cout][cin][9][4][4] spin matrices (interleaved re, im), layers one after the
+ * other.  The network is not part of the paper. */
+int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch);
+
+/* Kernel profiling for benchmarks (not part of the paper).  mode 0: off;
+ * 1: count the library's kernel launches by class; 2: also time each launch with
+ * a CUDA event pair recorded on its launching stream.  Every call resets the
+ * counters.  Timing adds two event records per launch and nothing else. */
+int qxd_profile(qxd_ctx* ctx, int mode);
+
+/* Class i (0-based, in order of first launch) of the profile: its name, launch
+ * count, summed device time in ms (mode 2; synchronises the recorded events)
+ * and summed algorithmic DRAM bytes (every input and output array element
+ * counted once per launch: the roofline numerator).  QXD_EARG past the last class. */
+int qxd_profile_entry(qxd_ctx* ctx, int i, char* name, int len, long long* launches, double* ms, double* bytes);
+
+/* Message describing the last failing call on ctx (never NULL). */
+const char* qxd_last_error(qxd_ctx* ctx);
+
+/* Number of simulated sites V of the context (0 for NULL). */
+long long qxd_volume(const qxd_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QXD_H */

@@ -1,0 +1,42 @@
+// Vector-kernel interface used by the solvers (blas.cu).  Fields are flat
+// arrays of n complex numbers in precision 0 (FP64), 1 (FP32) or 2 (BF16).
+// Reductions write their FP64 results to ctx->red_result[slot ...]; blas_fetch
+// copies the first nslots results to ctx->red_host and synchronises the stream.
+#pragma once
+
+#include "qxd_internal.h"
+
+namespace qxd {
+
+constexpr int kMultiMax = 8;
+constexpr int kRedSlots = 512;
+constexpr int kPartials = 16 * 1024;
+
+struct MultiPtr {
+    const void* p[kMultiMax];
+};
+struct MultiCoef {
+    double re[kMultiMax];
+    double im[kMultiMax];
+};
+
+// Same-precision operations treat a field as a flat array (any n); operations
+// between two precisions work site by site on whole half-lattice fields
+// (n a multiple of 12 V/2), because the flat complex order of the internal
+// layout depends on the precision.
+// result[slot], result[slot+1] = Re, Im <a, b> = sum conj(a) b (pa == pb)
+int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* b, int slot, cudaStream_t st);
+// result[slot] = |a|^2 over finite entries, result[slot+1] = number of non-finite entries
+int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st);
+// result[slot + 2j], [slot + 2j + 1] = <W_j, v>, j < k
+int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, const void* v, int slot,
+                   cudaStream_t st);
+// y = a x + b y
+int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, const void* x, double br, double bi,
+               void* y, cudaStream_t st);
+// y += sum_j c_j X_j  (px == py)
+int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
+                    const void* const* X, void* y, cudaStream_t st);
+int blas_fetch(qxd_ctx* ctx, int nslots, cudaStream_t st);
+
+}  // namespace qxd

@@ -1,0 +1,35 @@
+// Operator compositions built from the hopping and site-diagonal kernels.
+#pragma once
+
+#include "qxd_internal.h"
+
+namespace qxd {
+
+// a full-lattice field as its even and odd halves (internal layout)
+struct Full {
+    void* e;
+    void* o;
+};
+
+// bytes of one half-lattice field in precision P (0 FP64, 1 FP32, 2 BF16)
+size_t half_bytes(const qxd_ctx* ctx, int P);
+
+// out = D in (eq. dirac):  out_e = A_ee in_e + H_eo in_o,  out_o = A_oo in_o + H_oe in_e
+int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStream_t st, int nrhs = 1);
+// out_e = Dhat in_e = A_ee in_e - H_eo A_oo^-1 H_oe in_e (dagger: gamma5 Dhat gamma5); tmp_o: odd scratch
+int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out_e, void* tmp_o, cudaStream_t st,
+            int nrhs = 1);
+// b_e = r_e - H_eo A_oo^-1 r_o  (even-odd preconditioned source)
+int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st);
+// x_o = A_oo^-1 (r_o - H_oe x_e)
+int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void* x_e, void* x_o, cudaStream_t st);
+// z = M r (identity or the learned preconditioner)
+int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z, cudaStream_t st);
+
+// solvers.cu
+int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
+                 cudaStream_t st);
+int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
+                  cudaStream_t st);
+
+}  // namespace qxd

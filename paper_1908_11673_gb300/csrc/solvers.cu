@@ -1,0 +1,308 @@
+// Solvers (Sec. 4.4): CG on the normal equations of the even-odd operator
+// (CGNE), flexible GCR on Dhat inside FP64 defect correction, and the
+// multi-shift CG of the rational approximation (App. A.2).  Host loops drive
+// the kernels; scalars come back to the host once or twice per iteration.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "blas.h"
+#include "ops.h"
+#include "qxd_internal.h"
+
+namespace qxd {
+
+// QXD_VERBOSE=1 in the environment prints the solver scalars to stderr
+static bool verbose() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("QXD_VERBOSE");
+        v = (e && *e && *e != '0') ? 1 : 0;
+    }
+    return v == 1;
+}
+
+static int status_of_norm(qxd_ctx* ctx, double nonfinite, const char* where) {
+    if (nonfinite != 0.0) return qxd_fail(ctx, QXD_ENAN, std::string("non-finite value in ") + where);
+    return QXD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// r = eta - D x (FP64, full lattice); returns |r|^2 in *rr
+int full_residual64(qxd_ctx* ctx, int fl, const Full& eta, const Full& x, const Full& r, const Full& tmp_o,
+                    double* rr, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    // r = D x, then r = eta - r
+    QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, r, st));
+    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.e, -1.0, 0.0, r.e, st));
+    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.o, -1.0, 0.0, r.o, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, r.e, 0, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, r.o, 2, st));
+    QXD_TRY(blas_fetch(ctx, 4, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "residual"));
+    *rr = ctx->red_host[0] + ctx->red_host[2];
+    (void)tmp_o;
+    return QXD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CGNE (FP64): even-odd system, CG on Dhat^+ Dhat tracking s = eta_hat - Dhat y.
+int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
+                 cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, QXD_FP64);
+    void *b, *sv, *z, *p, *w, *to, *re, *ro, *de, *dO;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 0, hb, &b));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 1, hb, &sv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 2, hb, &z));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 3, hb, &p));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 4, hb, &w));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 5, hb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 6, hb, &re));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 7, hb, &ro));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 8, hb, &de));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 9, hb, &dO));
+    Full r{re, ro}, dx{de, dO};
+    // |eta|
+    QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
+    QXD_TRY(blas_fetch(ctx, 4, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "source"));
+    const double enorm = std::sqrt(ctx->red_host[0] + ctx->red_host[2]);
+    QXD_CUDA(ctx, cudaMemsetAsync(x.e, 0, hb, st));
+    QXD_CUDA(ctx, cudaMemsetAsync(x.o, 0, hb, st));
+    info->iters = 0;
+    info->op_applies = 0;
+    info->restarts = 0;
+    info->true_relres = 1.0;
+    if (enorm == 0.0) {
+        info->true_relres = 0.0;
+        return QXD_OK;
+    }
+    // r = eta (x = 0)
+    QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb, cudaMemcpyDeviceToDevice, st));
+    const double target = 0.5 * s->tol * enorm;
+    for (int restart = 0; restart < 8; ++restart) {
+        // eta_hat = r_e - H_eo A_oo^-1 r_o
+        QXD_TRY(op_eo_source(ctx, fl, QXD_FP64, r, b, to, st));
+        // CGNR on Dhat y = b, y = 0
+        QXD_CUDA(ctx, cudaMemsetAsync(dx.e, 0, hb, st));
+        QXD_CUDA(ctx, cudaMemcpyAsync(sv, b, hb, cudaMemcpyDeviceToDevice, st));
+        QXD_TRY(op_Dhat(ctx, fl, QXD_FP64, 1, sv, z, to, st));
+        QXD_CUDA(ctx, cudaMemcpyAsync(p, z, hb, cudaMemcpyDeviceToDevice, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, z, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        double zz = ctx->red_host[0];
+        info->op_applies += 1;
+        while (true) {
+            if (info->iters >= s->nmx) break;
+            QXD_TRY(op_Dhat(ctx, fl, QXD_FP64, 0, p, w, to, st));
+            QXD_TRY(blas_norm2(ctx, 0, n, w, 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "CGNE"));
+            const double ww = ctx->red_host[0];
+            info->iters += 1;
+            info->op_applies += 1;
+            if (ww == 0.0) return qxd_fail(ctx, QXD_EBREAKDOWN, "CGNE: |Dhat p| = 0");
+            const double alpha = zz / ww;
+            QXD_TRY(blas_axpby(ctx, 0, 0, n, alpha, 0.0, p, 1.0, 0.0, dx.e, st));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n, -alpha, 0.0, w, 1.0, 0.0, sv, st));
+            QXD_TRY(op_Dhat(ctx, fl, QXD_FP64, 1, sv, z, to, st));
+            info->op_applies += 1;
+            QXD_TRY(blas_norm2(ctx, 0, n, sv, 0, st));
+            QXD_TRY(blas_norm2(ctx, 0, n, z, 2, st));
+            QXD_TRY(blas_fetch(ctx, 4, st));
+            const double ss = ctx->red_host[0];
+            const double zz_new = ctx->red_host[2];
+            if (verbose() && (info->iters % 50 == 0))
+                std::fprintf(stderr, "[qxd cgne] it %d |s|/|eta| %.6e\n", info->iters, std::sqrt(ss) / enorm);
+            if (std::sqrt(ss) <= target) break;
+            const double beta = zz_new / zz;
+            zz = zz_new;
+            QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, z, beta, 0.0, p, st));
+        }
+        // dx_o = A_oo^-1 (r_o - H_oe dx_e);  x += dx
+        QXD_TRY(op_odd_reconstruct(ctx, fl, QXD_FP64, r.o, dx.e, dx.o, st));
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.e, 1.0, 0.0, x.e, st));
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.o, 1.0, 0.0, x.o, st));
+        double rr;
+        QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{to, to}, &rr, st));
+        info->op_applies += 1;
+        info->true_relres = std::sqrt(rr) / enorm;
+        if (info->true_relres <= s->tol) return QXD_OK;
+        if (info->iters >= s->nmx) break;
+        info->restarts += 1;
+    }
+    return qxd_fail(ctx, QXD_ENOCONV, "CGNE: tolerance not reached within nmx");
+}
+
+// ---------------------------------------------------------------------------
+// Flexible GCR on Dhat in precision P (even-site vectors), right preconditioner M.
+// Solves Dhat e = b to |b - Dhat e| <= rtol |b|; e is overwritten.
+int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, void* e, int max_iter,
+               double rtol, int* iters, cudaStream_t st) {
+    const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *r, *to, *tmp;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 20, hb, &r));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 21, hb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 22, hb, &tmp));
+    std::vector<void*> Z(nkv), W(nkv);
+    for (int k = 0; k < nkv; ++k) {
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 24 + 2 * k, hb, &Z[k]));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 25 + 2 * k, hb, &W[k]));
+    }
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_TRY(blas_fetch(ctx, 2, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "GCR source"));
+    const double bn = std::sqrt(ctx->red_host[0]);
+    *iters = 0;
+    if (bn == 0.0) return QXD_OK;
+    double rr = bn * bn;
+    std::vector<double> Rre(nkv * nkv), Rim(nkv * nkv), are(nkv), aim(nkv), ww(nkv), cre(nkv), cim(nkv);
+    std::vector<const void*> Wc(nkv + 1);
+    bool done = false;
+    while (!done && *iters < max_iter) {
+        int K = 0;
+        for (int k = 0; k < nkv; ++k) {
+            QXD_TRY(apply_precond(ctx, fl, P, s->precond, r, Z[k], st));
+            QXD_TRY(op_Dhat(ctx, fl, P, 0, Z[k], W[k], to, st));
+            // <W_j, w_k> for j < k, and <r, w_k>
+            for (int j = 0; j < k; ++j) Wc[j] = W[j];
+            Wc[k] = r;
+            QXD_TRY(blas_multi_dot(ctx, P, n, k + 1, Wc.data(), W[k], 0, st));
+            QXD_TRY(blas_fetch(ctx, 2 * (k + 1), st));
+            for (int j = 0; j < k; ++j) {
+                Rre[j * nkv + k] = ctx->red_host[2 * j] / ww[j];
+                Rim[j * nkv + k] = ctx->red_host[2 * j + 1] / ww[j];
+                cre[j] = -Rre[j * nkv + k];
+                cim[j] = -Rim[j * nkv + k];
+            }
+            // <w_k, r> = conj(<r, w_k>); r is orthogonal to the earlier w_j
+            const double wr_re = ctx->red_host[2 * k], wr_im = -ctx->red_host[2 * k + 1];
+            if (k > 0) {
+                std::vector<const void*> Wp(W.begin(), W.begin() + k);
+                QXD_TRY(blas_multi_axpy(ctx, P, P, n, k, cre.data(), cim.data(), Wp.data(), W[k], st));
+            }
+            QXD_TRY(blas_norm2(ctx, P, n, W[k], 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            ww[k] = ctx->red_host[0];
+            if (verbose())
+                std::fprintf(stderr, "[qxd gcr] it %d k %d |w|^2 %.6e <w,r> (%.6e, %.6e) rr %.6e nonfinite %g\n", *iters,
+                             k, ww[k], wr_re, wr_im, rr, ctx->red_host[1]);
+            QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "GCR"));
+            if (!(ww[k] > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
+            are[k] = wr_re / ww[k];
+            aim[k] = wr_im / ww[k];
+            QXD_TRY(blas_axpby(ctx, P, P, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
+            rr -= (wr_re * wr_re + wr_im * wr_im) / ww[k];
+            *iters += 1;
+            K = k + 1;
+            if (rr <= rtol * rtol * bn * bn || *iters >= max_iter) {
+                done = true;
+                break;
+            }
+        }
+        // back substitution: c_j = a_j - sum_{k>j} R_jk c_k
+        for (int j = K - 1; j >= 0; --j) {
+            double sr = are[j], si = aim[j];
+            for (int k = j + 1; k < K; ++k) {
+                const double rr_ = Rre[j * nkv + k], ri = Rim[j * nkv + k];
+                sr -= rr_ * cre[k] - ri * cim[k];
+                si -= rr_ * cim[k] + ri * cre[k];
+            }
+            cre[j] = sr;
+            cim[j] = si;
+        }
+        std::vector<const void*> Zp(Z.begin(), Z.begin() + K);
+        QXD_TRY(blas_multi_axpy(ctx, P, P, n, K, cre.data(), cim.data(), Zp.data(), e, st));
+        if (!done) {
+            // restart: r = b - Dhat e
+            QXD_TRY(op_Dhat(ctx, fl, P, 0, e, tmp, to, st));
+            QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
+            QXD_TRY(blas_axpby(ctx, P, P, n, -1.0, 0.0, tmp, 1.0, 0.0, r, st));
+            QXD_TRY(blas_norm2(ctx, P, n, r, 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            rr = ctx->red_host[0];
+            if (rr <= rtol * rtol * bn * bn) done = true;
+        }
+    }
+    return QXD_OK;
+}
+
+// FP64 defect correction around inner FGCR solves in precision s->inner.
+int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
+                  cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const int P = s->inner;
+    const size_t hb64 = half_bytes(ctx, QXD_FP64);
+    const size_t hbP = half_bytes(ctx, P);
+    void *re, *ro, *t64, *bP, *roP, *tP, *eeP, *eoP, *to2;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 10, hb64, &re));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 11, hb64, &ro));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 12, hb64, &t64));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 13, hbP, &bP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 14, hbP, &roP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 15, hbP, &tP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 16, hbP, &eeP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 17, hbP, &eoP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 18, hbP, &to2));
+    Full r{re, ro};
+    QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
+    QXD_TRY(blas_fetch(ctx, 4, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "source"));
+    const double enorm = std::sqrt(ctx->red_host[0] + ctx->red_host[2]);
+    QXD_CUDA(ctx, cudaMemsetAsync(x.e, 0, hb64, st));
+    QXD_CUDA(ctx, cudaMemsetAsync(x.o, 0, hb64, st));
+    info->iters = 0;
+    info->op_applies = 0;
+    info->restarts = 0;
+    info->true_relres = 1.0;
+    if (enorm == 0.0) {
+        info->true_relres = 0.0;
+        return QXD_OK;
+    }
+    QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb64, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb64, cudaMemcpyDeviceToDevice, st));
+    double relres = 1.0;
+    const double itol = s->inner_tol > 0 ? s->inner_tol : (P == QXD_BF16 ? 5e-3 : (P == QXD_FP32 ? 1e-5 : 1e-10));
+    for (int outer = 0; outer < 64; ++outer) {
+        if (outer > 0) {
+            double rr;
+            QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
+            info->op_applies += 1;
+            relres = std::sqrt(rr) / enorm;
+            info->true_relres = relres;
+            if (verbose()) std::fprintf(stderr, "[qxd dc] outer %d true relres %.6e\n", outer, relres);
+            if (relres <= s->tol) return QXD_OK;
+            info->restarts += 1;
+        }
+        if (info->iters >= s->nmx) break;
+        // even-odd source in precision P: b = r_e - H_eo A_oo^-1 r_o
+        QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, r.e, 0.0, 0.0, tP, st));
+        QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, r.o, 0.0, 0.0, roP, st));
+        QXD_TRY(op_eo_source(ctx, fl, P, Full{tP, roP}, bP, to2, st));
+        int it = 0;
+        const double rtol = std::max(itol, 0.5 * s->tol / relres);
+        QXD_TRY(fgcr_inner(ctx, fl, P, s, bP, eeP, s->nmx - info->iters, rtol, &it, st));
+        info->iters += it;
+        info->op_applies += it + 2;
+        // e_o = A_oo^-1 (r_o - H_oe e_e);  x += e
+        QXD_TRY(op_odd_reconstruct(ctx, fl, P, roP, eeP, eoP, st));
+        QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
+        QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+    }
+    double rr;
+    QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
+    info->true_relres = std::sqrt(rr) / enorm;
+    if (info->true_relres <= s->tol) return QXD_OK;
+    return qxd_fail(ctx, QXD_ENOCONV, "FGCR: tolerance not reached within nmx");
+}
+
+}  // namespace qxd

@@ -1,0 +1,212 @@
+"""Thin ctypes binding of libqxd (include/qxd.h): argument marshalling only.
+
+Arrays may be NumPy arrays (host memory) or CUDA torch tensors (device memory);
+the library itself decides whether to stage them.  Every function raises
+QxdError when the C call returns a non-zero status.  There is no fallback: if
+libqxd.so has not been built (``paper_1908_11673_gb300.build``) or no CUDA
+device is present, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libqxd.so")
+
+FP64, FP32, BF16 = 0, 1, 2
+CGNE, FGCR, MSCG = 0, 1, 2
+PRECOND_NONE, PRECOND_LEARNED = 0, 1
+
+STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: "QXD_ENAN",
+          5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
+
+EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_apply_Dw",
+           "qxd_apply_Dhat_eo", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
+           "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
+
+
+class QxdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("cstar", ctypes.c_int), ("theta", ctypes.c_double * 4)]
+
+
+class Flavour(ctypes.Structure):
+    _fields_ = [("qhat", ctypes.c_int), ("kappa", ctypes.c_double), ("su3csw", ctypes.c_double),
+                ("u1csw", ctypes.c_double)]
+
+
+class Solver(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("tol", ctypes.c_double), ("nmx", ctypes.c_int), ("nkv", ctypes.c_int),
+                ("inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("op_applies", ctypes.c_int), ("true_relres", ctypes.c_double)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIBPATH) -> ctypes.CDLL:
+    """Load libqxd.so and declare its signatures (raises OSError if absent)."""
+    global _lib
+    if _lib is not None and path == LIBPATH:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with `python -m paper_1908_11673_gb300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "qxd_create": (i, [ctypes.POINTER(Geom), i, ctypes.POINTER(vp)]),
+        "qxd_destroy": (None, [vp]),
+        "qxd_set_links": (i, [vp, vp, vp, d, vp]),
+        "qxd_set_clover": (i, [vp, i, ctypes.POINTER(Flavour), vp]),
+        "qxd_apply_Dw": (i, [vp, i, i, vp, vp, i, vp]),
+        "qxd_apply_Dhat_eo": (i, [vp, i, i, i, vp, vp, i, vp]),
+        "qxd_solve": (i, [vp, i, ctypes.POINTER(Solver), vp, vp, i, ctypes.POINTER(Info), vp]),
+        "qxd_solve_multishift": (i, [vp, i, i, vp, ctypes.POINTER(Solver), vp, vp, ctypes.POINTER(Info), vp]),
+        "qxd_set_precond_weights": (i, [vp, i, vp, i, i]),
+        "qxd_profile": (i, [vp, i]),
+        "qxd_profile_entry": (i, [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "qxd_last_error": (ctypes.c_char_p, [vp]),
+        "qxd_volume": (ctypes.c_longlong, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    if path == LIBPATH:
+        _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a NumPy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    return int(s)
+
+
+class Context:
+    """One lattice on one GPU (qxd_create ... qxd_destroy)."""
+
+    def __init__(self, L, cstar=0, theta=(0.0, 0.0, 0.0, 0.0), device=0):
+        self.lib = load_library()
+        g = Geom()
+        g.L[:] = [int(v) for v in L]
+        g.cstar = int(cstar)
+        g.theta[:] = [float(t) for t in theta]
+        self._h = ctypes.c_void_p()
+        rc = self.lib.qxd_create(ctypes.byref(g), int(device), ctypes.byref(self._h))
+        if rc != 0:
+            raise QxdError(rc, "qxd_create failed (geometry or device)")
+        self.L = tuple(int(v) for v in L)
+        self.cstar = int(cstar)
+        self.V = int(self.lib.qxd_volume(self._h))
+        self.Vh = self.V // 2
+
+    def _check(self, rc):
+        if rc != 0:
+            raise QxdError(rc, self.lib.qxd_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.qxd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_links(self, U, A, invqel=6.0, stream=None):
+        self._check(self.lib.qxd_set_links(self._h, _ptr(U), _ptr(A), float(invqel), _stream(stream)))
+
+    def set_clover(self, fl, qhat, kappa, su3csw, u1csw, stream=None):
+        f = Flavour(int(qhat), float(kappa), float(su3csw), float(u1csw))
+        self._check(self.lib.qxd_set_clover(self._h, int(fl), ctypes.byref(f), _stream(stream)))
+
+    def apply_Dw(self, fl, prec, inp, out, nrhs=1, stream=None):
+        self._check(self.lib.qxd_apply_Dw(self._h, int(fl), int(prec), _ptr(inp), _ptr(out), int(nrhs),
+                                          _stream(stream)))
+
+    def apply_Dhat_eo(self, fl, prec, inp, out, dagger=False, nrhs=1, stream=None):
+        self._check(self.lib.qxd_apply_Dhat_eo(self._h, int(fl), int(prec), int(bool(dagger)), _ptr(inp),
+                                               _ptr(out), int(nrhs), _stream(stream)))
+
+    def solve(self, fl, eta, psi, kind=FGCR, tol=1e-10, nmx=20000, nkv=16, inner=FP32, inner_tol=0.0,
+              precond=PRECOND_NONE, nrhs=1, stream=None, check=True):
+        s = Solver(int(kind), float(tol), int(nmx), int(nkv), int(inner), float(inner_tol), int(precond))
+        info = Info()
+        rc = self.lib.qxd_solve(self._h, int(fl), ctypes.byref(s), _ptr(eta), _ptr(psi), int(nrhs),
+                                ctypes.byref(info), _stream(stream))
+        if check:
+            self._check(rc)
+        return info
+
+    def solve_multishift(self, fl, sigma, phi_e, x_e, tol=1e-10, nmx=20000, inner=FP64, stream=None,
+                         check=True):
+        sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+        s = Solver(MSCG, float(tol), int(nmx), 0, int(inner), 0.0, PRECOND_NONE)
+        info = Info()
+        rc = self.lib.qxd_solve_multishift(self._h, int(fl), len(sig), sig.ctypes.data, ctypes.byref(s),
+                                           _ptr(phi_e), _ptr(x_e), ctypes.byref(info), _stream(stream))
+        if check:
+            self._check(rc)
+        return info
+
+    def profile(self, mode):
+        """0 off, 1 count kernel launches, 2 count and time them (resets the counters)."""
+        self._check(self.lib.qxd_profile(self._h, int(mode)))
+
+    def profile_entries(self):
+        """[{name, launches, ms, bytes}] for every kernel class launched since profile()."""
+        out = []
+        buf = ctypes.create_string_buffer(64)
+        n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+        i = 0
+        while self.lib.qxd_profile_entry(self._h, i, buf, 64, ctypes.byref(n), ctypes.byref(ms),
+                                         ctypes.byref(by)) == 0:
+            out.append({"name": buf.value.decode(), "launches": n.value, "ms": ms.value, "bytes": by.value})
+            i += 1
+        return out
+
+    def set_precond_weights(self, fl, W, nlayers, nch):
+        self._check(self.lib.qxd_set_precond_weights(self._h, int(fl), _ptr(W), int(nlayers), int(nch)))

@@ -1,0 +1,100 @@
+"""GPU parity of the operator applications against the FP64 oracle.
+
+Tolerances (norm-relative over the whole output):
+  FP64              1e-13 (operator parity bar);
+  FP32              2e-6: inputs, links and site-diagonal terms are rounded to
+                    binary32 (2^-24 relative each) and each output component sums
+                    ~10^2 products of O(1) terms; observed errors are a few 1e-7;
+  BF16 spinors      2e-2: input and output spinors are rounded to bfloat16
+                    (2^-9 relative), the arithmetic is FP32.
+"""
+import numpy as np
+import pytest
+
+from oracle.dirac import gamma5
+from paper_1908_11673_gb300 import workload
+from tests.gpu_helpers import relerr, setup
+
+pytestmark = pytest.mark.gpu
+
+GEOMS = [
+    ((6, 4, 4, 6), 0, (np.pi, 0.0, 0.0, 0.0), -2),
+    ((4, 6, 4, 8), 0, (0.3, 0.7, -1.1, 2.0), 4),
+    ((4, 4, 6, 4), 1, (np.pi, 0.0, 0.0, 0.0), 4),
+    ((6, 4, 6, 4), 2, (np.pi, 0.0, 0.0, 0.0), -2),
+    ((4, 6, 4, 4), 3, (np.pi, 0.0, 0.0, 0.0), 1),
+    ((8, 8, 8, 8), 0, (np.pi, 0.0, 0.0, 0.0), -2),
+]
+TOL = {0: 1e-13, 1: 2e-6, 2: 2e-2}
+
+
+@pytest.mark.parametrize("L,cstar,theta,qhat", GEOMS)
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_apply_Dw_parity(L, cstar, theta, qhat, prec):
+    qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=qhat, seed=1000 + sum(L))
+    psi = workload.spinor(op.geom.V, 5)
+    if prec != 0:
+        psi = psi.astype(np.complex64)
+    out = np.empty_like(psi)
+    ctx.apply_Dw(0, prec, psi, out)
+    ref = op.apply(psi.astype(np.complex128))
+    assert relerr(out.astype(np.complex128), ref) <= TOL[prec]
+    ctx.close()
+
+
+@pytest.mark.parametrize("L,cstar,theta,qhat", GEOMS)
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_Dhat_parity(L, cstar, theta, qhat, prec, dagger):
+    qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=qhat, seed=2000 + sum(L))
+    ne = op.geom.V // 2
+    psi = workload.spinor(ne, 6)
+    if prec != 0:
+        psi = psi.astype(np.complex64)
+    out = np.empty_like(psi)
+    ctx.apply_Dhat_eo(0, prec, psi, out, dagger=dagger)
+    p = psi.astype(np.complex128)
+    ref = gamma5(op.Dhat(gamma5(p))) if dagger else op.Dhat(p)
+    assert relerr(out.astype(np.complex128), ref) <= TOL[prec]
+    ctx.close()
+
+
+def test_apply_Dw_multiple_rhs_and_device_buffers():
+    qxd, ctx, op, _, _ = setup((4, 4, 6, 4), 1, (np.pi, 0, 0, 0), qhat=4)
+    import torch
+    V = op.geom.V
+    psi = workload.spinor(V, 9, nrhs=3)
+    d_in = torch.from_numpy(psi).cuda()
+    d_out = torch.empty_like(d_in)
+    ctx.apply_Dw(0, 0, d_in, d_out, nrhs=3)
+    torch.cuda.synchronize()
+    out = d_out.cpu().numpy()
+    for r in range(3):
+        assert relerr(out[r], op.apply(psi[r])) <= 1e-13
+    ctx.close()
+
+
+def test_full_size_sampled_parity():
+    """32^3 x 64 physical lattice with C* in 3 directions (extended 64x64x32x32,
+    V = 4,194,304), stout-smeared links, qhat = 4: FP64 and FP32 outputs at 3000
+    sampled sites against the oracle evaluated at those sites only."""
+    import torch
+    L = (64, 32, 32, 32)
+    qxd, ctx, op, _, _ = setup(L, 3, (np.pi, 0, 0, 0), qhat=4, kappa=0.137312, seed=2000, stout=5,
+                               device="cuda")
+    V = op.geom.V
+    assert V == 4194304
+    psi = workload.spinor(V, 2001)
+    sites = np.random.default_rng(0).choice(V, 3000, replace=False)
+    ref = op.apply(psi, sites)
+    d_in = torch.from_numpy(psi).cuda()
+    d_out = torch.empty_like(d_in)
+    ctx.apply_Dw(0, 0, d_in, d_out)
+    out = d_out.cpu().numpy()
+    assert relerr(out[sites], ref) <= 1e-13
+    d_in32 = d_in.to(torch.complex64)
+    d_out32 = torch.empty_like(d_in32)
+    ctx.apply_Dw(0, 1, d_in32, d_out32)
+    ref32 = op.apply(d_in32.cpu().numpy().astype(np.complex128), sites)
+    assert relerr(d_out32.cpu().numpy()[sites].astype(np.complex128), ref32) <= TOL[1]
+    ctx.close()
