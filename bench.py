@@ -47,7 +47,10 @@ WORKLOADS = {
     "32^3x64-cstar3": dict(L=(64, 32, 32, 32), cstar=3, theta=(math.pi, 0.0, 0.0, 0.0), qhat=4,
                            kappa=0.137312, su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=2000,
                            src_seed=2001, stout=5, rho=0.1),
-    # small case for profiler captures and quick checks (8^4, antiperiodic time)
+    # 24^3 x 48, antiperiodic time (larger than L2, a few GB on the device: profiler captures)
+    "24^3x48": dict(L=(48, 24, 24, 24), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,
+                    su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=3000, src_seed=3001, stout=5, rho=0.1),
+    # small case for quick checks (8^4, antiperiodic time)
     "8^4": dict(L=(8, 8, 8, 8), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,
                 su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=1000, src_seed=1001, stout=0, rho=0.1),
     "16^4": dict(L=(16, 16, 16, 16), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,

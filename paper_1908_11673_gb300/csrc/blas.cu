@@ -2,40 +2,63 @@
 // deterministic reductions (block partial sums, then one block sums the
 // partials in a fixed order; every sum is accumulated in FP64).
 //
-// A field is handled here as a flat array of n complex numbers: the
-// structure-of-arrays chunks of the internal layout store (re, im) pairs
-// contiguously in every precision (double2, two float2 per float4, two
-// bfloat16 per 32-bit word).
+// Within one precision a field is handled as a flat array of n complex numbers
+// (the structure-of-arrays chunks store (re, im) pairs contiguously); operations
+// between two precisions go site by site through the layout-aware spinor access.
 #include "qxd_internal.h"
 #include "blas.h"
 
 namespace qxd {
 
-template <int P> struct Elem;
-template <> struct Elem<0> {
+// Flat access in 16-byte chunks: one complex (FP64), two (FP32) or four (BF16)
+// per chunk.  Arithmetic runs in the storage precision's real type (FP32 for
+// FP32 and BF16 data: the FP64 pipe of this GPU is 1/64 of the FP32 one);
+// reductions add FP32 partial sums of at most kFlush chunks into FP64 accumulators.
+template <int P> struct Chunk;
+template <> struct Chunk<0> {
     using R = double;
-    static QXD_HD cplx<double> ld(const void* p, size_t i) {
+    static constexpr int NC = 1;
+    static QXD_HD void ld(const void* p, size_t i, cplx<double> c[1]) {
         double2 v = QXD_LDG(static_cast<const double2*>(p) + i);
-        return {v.x, v.y};
+        c[0] = {v.x, v.y};
     }
-    static QXD_HD void st(void* p, size_t i, cplx<double> v) { static_cast<double2*>(p)[i] = make_double2(v.re, v.im); }
+    static QXD_HD void st(void* p, size_t i, const cplx<double> c[1]) {
+        static_cast<double2*>(p)[i] = make_double2(c[0].re, c[0].im);
+    }
 };
-template <> struct Elem<1> {
+template <> struct Chunk<1> {
     using R = float;
-    static QXD_HD cplx<float> ld(const void* p, size_t i) {
-        float2 v = QXD_LDG(static_cast<const float2*>(p) + i);
-        return {v.x, v.y};
+    static constexpr int NC = 2;
+    static QXD_HD void ld(const void* p, size_t i, cplx<float> c[2]) {
+        float4 v = QXD_LDG(static_cast<const float4*>(p) + i);
+        c[0] = {v.x, v.y};
+        c[1] = {v.z, v.w};
     }
-    static QXD_HD void st(void* p, size_t i, cplx<float> v) { static_cast<float2*>(p)[i] = make_float2(v.re, v.im); }
+    static QXD_HD void st(void* p, size_t i, const cplx<float> c[2]) {
+        static_cast<float4*>(p)[i] = make_float4(c[0].re, c[0].im, c[1].re, c[1].im);
+    }
 };
-template <> struct Elem<2> {
+template <> struct Chunk<2> {
     using R = float;
-    static QXD_HD cplx<float> ld(const void* p, size_t i) {
-        uint32_t v = QXD_LDG(static_cast<const uint32_t*>(p) + i);
-        return {bf16_lo(v), bf16_hi(v)};
+    static constexpr int NC = 4;
+    static QXD_HD void ld(const void* p, size_t i, cplx<float> c[4]) {
+        uint4 v = QXD_LDG(static_cast<const uint4*>(p) + i);
+        c[0] = {bf16_lo(v.x), bf16_hi(v.x)};
+        c[1] = {bf16_lo(v.y), bf16_hi(v.y)};
+        c[2] = {bf16_lo(v.z), bf16_hi(v.z)};
+        c[3] = {bf16_lo(v.w), bf16_hi(v.w)};
     }
-    static QXD_HD void st(void* p, size_t i, cplx<float> v) { static_cast<uint32_t*>(p)[i] = pack_bf16x2(v.re, v.im); }
+    static QXD_HD void st(void* p, size_t i, const cplx<float> c[4]) {
+        uint4 v;
+        v.x = pack_bf16x2(c[0].re, c[0].im);
+        v.y = pack_bf16x2(c[1].re, c[1].im);
+        v.z = pack_bf16x2(c[2].re, c[2].im);
+        v.w = pack_bf16x2(c[3].re, c[3].im);
+        static_cast<uint4*>(p)[i] = v;
+    }
 };
+
+constexpr int kFlush = 8;
 
 constexpr int kRedThreads = 256;
 constexpr int kMaxRedBlocks = 1024;
@@ -101,76 +124,128 @@ static int finish(qxd_ctx* ctx, int nb, int ncomp, int slot, cudaStream_t st) {
 }
 
 // ---- reductions ---------------------------------------------------------------
-template <int PA, int PB>
-__global__ void __launch_bounds__(kRedThreads) k_dot(size_t n, const void* __restrict__ a, const void* __restrict__ b,
-                                                     double* __restrict__ partials) {
+// n counts complex numbers; every kernel walks over n / NC chunks.
+template <int P>
+__global__ void __launch_bounds__(kRedThreads) k_dot(size_t nch, const void* __restrict__ a,
+                                                     const void* __restrict__ b, double* __restrict__ partials) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
     double v[2] = {0.0, 0.0};
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        auto x = Elem<PA>::ld(a, i);
-        auto y = Elem<PB>::ld(b, i);
-        const double xr = x.re, xi = x.im, yr = y.re, yi = y.im;
-        v[0] += xr * yr + xi * yi;
-        v[1] += xr * yi - xi * yr;
+    R f[2] = {R(0), R(0)};
+    int cnt = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> x[NC], y[NC];
+        Chunk<P>::ld(a, i, x);
+        Chunk<P>::ld(b, i, y);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            f[0] = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, f[0]));
+            f[1] = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, f[1]));
+        }
+        if (++cnt == kFlush) {
+            v[0] += f[0]; v[1] += f[1];
+            f[0] = f[1] = R(0);
+            cnt = 0;
+        }
     }
+    v[0] += f[0];
+    v[1] += f[1];
     block_reduce_store<2>(v, partials);
 }
 
 template <int P>
-__global__ void __launch_bounds__(kRedThreads) k_norm2(size_t n, const void* __restrict__ a,
+__global__ void __launch_bounds__(kRedThreads) k_norm2(size_t nch, const void* __restrict__ a,
                                                        double* __restrict__ partials) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
     double v[2] = {0.0, 0.0};  // |a|^2 and a count of non-finite entries
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        auto x = Elem<P>::ld(a, i);
-        const double xr = x.re, xi = x.im;
-        const double s = xr * xr + xi * xi;
-        if (isfinite(s)) v[0] += s;
-        else v[1] += 1.0;
+    R f = R(0);
+    int cnt = 0, bad = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> x[NC];
+        Chunk<P>::ld(a, i, x);
+        R s = R(0);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) s = fma(x[c].re, x[c].re, fma(x[c].im, x[c].im, s));
+        if (isfinite(s)) f += s;
+        else ++bad;
+        if (++cnt == kFlush) {
+            v[0] += f;
+            f = R(0);
+            cnt = 0;
+        }
     }
+    v[0] += f;
+    v[1] = bad;
     block_reduce_store<2>(v, partials);
 }
 
 // k dot products <W_j, v>, j < k (k <= kMultiMax)
 template <int P, int K>
-__global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t n, MultiPtr W, const void* __restrict__ v,
+__global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr W, const void* __restrict__ v,
                                                            double* __restrict__ partials) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
     double acc[2 * K];
+    R f[2 * K];
 #pragma unroll
-    for (int c = 0; c < 2 * K; ++c) acc[c] = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        auto y = Elem<P>::ld(v, i);
-        const double yr = y.re, yi = y.im;
+    for (int c = 0; c < 2 * K; ++c) {
+        acc[c] = 0.0;
+        f[c] = R(0);
+    }
+    int cnt = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> y[NC];
+        Chunk<P>::ld(v, i, y);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            auto x = Elem<P>::ld(W.p[j], i);
-            const double xr = x.re, xi = x.im;
-            acc[2 * j] += xr * yr + xi * yi;
-            acc[2 * j + 1] += xr * yi - xi * yr;
+            cplx<R> x[NC];
+            Chunk<P>::ld(W.p[j], i, x);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                f[2 * j] = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, f[2 * j]));
+                f[2 * j + 1] = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, f[2 * j + 1]));
+            }
+        }
+        if (++cnt == kFlush) {
+#pragma unroll
+            for (int c = 0; c < 2 * K; ++c) {
+                acc[c] += f[c];
+                f[c] = R(0);
+            }
+            cnt = 0;
         }
     }
+#pragma unroll
+    for (int c = 0; c < 2 * K; ++c) acc[c] += f[c];
     block_reduce_store<2 * K>(acc, partials);
 }
 
+static size_t nchunks(int P, size_t n) { return n / (P == 0 ? 1 : (P == 1 ? 2 : 4)); }
+
 int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* b, int slot, cudaStream_t st) {
-    const int nb = red_blocks(n);
-    {
-    ProfScope prof(ctx, "dot", (double)n * (eb(pa) + eb(pb)), st);
-#define QXD_DOT(A, B) k_dot<A, B><<<nb, kRedThreads, 0, st>>>(n, a, b, ctx->red_partials)
     // the flat complex order is the same only within one precision
-    if (pa == 0 && pb == 0) QXD_DOT(0, 0);
-    else if (pa == 1 && pb == 1) QXD_DOT(1, 1);
-    else if (pa == 2 && pb == 2) QXD_DOT(2, 2);
-    else return qxd_fail(ctx, QXD_EARG, "blas_dot: precisions must match");
-#undef QXD_DOT
+    if (pa != pb) return qxd_fail(ctx, QXD_EARG, "blas_dot: precisions must match");
+    const size_t nc = nchunks(pa, n);
+    const int nb = red_blocks(nc);
+    {
+        ProfScope prof(ctx, "dot", (double)n * (eb(pa) + eb(pb)), st);
+        if (pa == 0) k_dot<0><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
+        else if (pa == 1) k_dot<1><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
+        else k_dot<2><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
     }
     return finish(ctx, nb, 2, slot, st);
 }
 
 int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st) {
-    const int nb = red_blocks(n);
-    ProfScope prof(ctx, "norm2", (double)n * eb(p), st);
-    if (p == 0) k_norm2<0><<<nb, kRedThreads, 0, st>>>(n, a, ctx->red_partials);
-    else if (p == 1) k_norm2<1><<<nb, kRedThreads, 0, st>>>(n, a, ctx->red_partials);
-    else k_norm2<2><<<nb, kRedThreads, 0, st>>>(n, a, ctx->red_partials);
+    const size_t nc = nchunks(p, n);
+    const int nb = red_blocks(nc);
+    {
+        ProfScope prof(ctx, "norm2", (double)n * eb(p), st);
+        if (p == 0) k_norm2<0><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
+        else if (p == 1) k_norm2<1><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
+        else k_norm2<2><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
+    }
     return finish(ctx, nb, 2, slot, st);
 }
 
@@ -194,12 +269,13 @@ int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, c
         const int kk = (k - j0) < kMultiMax ? (k - j0) : kMultiMax;
         MultiPtr mp;
         for (int j = 0; j < kMultiMax; ++j) mp.p[j] = W[j0 + (j < kk ? j : 0)];
-        const int nb = red_blocks(n);
+        const size_t nc = nchunks(p, n);
+        const int nb = red_blocks(nc);
         {
         ProfScope prof(ctx, "multi_dot", (double)n * eb(p) * (kk + 1), st);
-        if (p == 0) multi_dot_k<0>(kk, nb, n, mp, v, ctx->red_partials, st);
-        else if (p == 1) multi_dot_k<1>(kk, nb, n, mp, v, ctx->red_partials, st);
-        else multi_dot_k<2>(kk, nb, n, mp, v, ctx->red_partials, st);
+        if (p == 0) multi_dot_k<0>(kk, nb, nc, mp, v, ctx->red_partials, st);
+        else if (p == 1) multi_dot_k<1>(kk, nb, nc, mp, v, ctx->red_partials, st);
+        else multi_dot_k<2>(kk, nb, nc, mp, v, ctx->red_partials, st);
         }
         QXD_TRY(finish(ctx, nb, 2 * kk, slot + 2 * j0, st));
     }
@@ -207,22 +283,25 @@ int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, c
 }
 
 // ---- updates -------------------------------------------------------------------
-// y = a*x + b*y  (x may be a different precision than y)
-template <int PX, int PY>
-__global__ void k_axpby(size_t n, double ar, double ai, const void* __restrict__ x, double br, double bi,
+// y = a*x + b*y (same precision, arithmetic in its real type)
+template <int P>
+__global__ void k_axpby(size_t nch, double ar, double ai, const void* __restrict__ x, double br, double bi,
                         void* __restrict__ y) {
-    using R = typename Elem<PY>::R;
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
     const cplx<R> a = {(R)ar, (R)ai}, b = {(R)br, (R)bi};
     const bool useb = !(br == 0.0 && bi == 0.0);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        auto xv = Elem<PX>::ld(x, i);
-        cplx<R> xx = {(R)xv.re, (R)xv.im};
-        cplx<R> r = a * xx;
-        if (useb) {
-            auto yv = Elem<PY>::ld(y, i);
-            r = r + b * cplx<R>{(R)yv.re, (R)yv.im};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> xv[NC], yv[NC];
+        Chunk<P>::ld(x, i, xv);
+        if (useb) Chunk<P>::ld(y, i, yv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cplx<R> r = a * xv[c];
+            if (useb) cmac(r, b, yv[c]);
+            yv[c] = r;
         }
-        Elem<PY>::st(y, i, r);
+        Chunk<P>::st(y, i, yv);
     }
 }
 
@@ -262,21 +341,25 @@ __global__ void k_axpby_site(int Vh, int nfields, double ar, double ai, const vo
     }
 }
 
-// y += sum_j c_j X_j  (k <= kMultiMax)
-template <int PX, int PY, int K>
-__global__ void k_multi_axpy(size_t n, MultiPtr X, MultiCoef c, void* __restrict__ y) {
-    using R = typename Elem<PY>::R;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        auto yv = Elem<PY>::ld(y, i);
-        double ar = yv.re, ai = yv.im;
+// y += sum_j c_j X_j  (k <= kMultiMax; same precision, arithmetic in its real type)
+template <int P, int K>
+__global__ void k_multi_axpy(size_t nch, MultiPtr X, MultiCoef c, void* __restrict__ y) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    cplx<R> cf[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) cf[j] = {(R)c.re[j], (R)c.im[j]};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> yv[NC];
+        Chunk<P>::ld(y, i, yv);
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            auto xv = Elem<PX>::ld(X.p[j], i);
-            const double xr = xv.re, xi = xv.im;
-            ar += c.re[j] * xr - c.im[j] * xi;
-            ai += c.re[j] * xi + c.im[j] * xr;
+            cplx<R> xv[NC];
+            Chunk<P>::ld(X.p[j], i, xv);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) cmac(yv[q], cf[j], xv[q]);
         }
-        Elem<PY>::st(y, i, cplx<R>{(R)ar, (R)ai});
+        Chunk<P>::st(y, i, yv);
     }
 }
 
@@ -291,10 +374,11 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
     const bool rb = !(br == 0.0 && bi == 0.0);
     ProfScope prof(ctx, px == py ? "axpby" : "axpby_convert", (double)n * (eb(px) + eb(py) * (rb ? 2 : 1)), st);
     if (px == py) {
-        const int nb = upd_blocks(ctx, n);
-        if (px == 0) k_axpby<0, 0><<<nb, 256, 0, st>>>(n, ar, ai, x, br, bi, y);
-        else if (px == 1) k_axpby<1, 1><<<nb, 256, 0, st>>>(n, ar, ai, x, br, bi, y);
-        else k_axpby<2, 2><<<nb, 256, 0, st>>>(n, ar, ai, x, br, bi, y);
+        const size_t nc = nchunks(px, n);
+        const int nb = upd_blocks(ctx, nc);
+        if (px == 0) k_axpby<0><<<nb, 256, 0, st>>>(nc, ar, ai, x, br, bi, y);
+        else if (px == 1) k_axpby<1><<<nb, 256, 0, st>>>(nc, ar, ai, x, br, bi, y);
+        else k_axpby<2><<<nb, 256, 0, st>>>(nc, ar, ai, x, br, bi, y);
     } else {
         const int Vh = ctx->g.Vh;
         if (n % (12ull * Vh) != 0) return qxd_fail(ctx, QXD_EARG, "blas_axpby: mixed precision needs whole fields");
@@ -313,23 +397,26 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
     return QXD_OK;
 }
 
-template <int PX, int PY>
-static void multi_axpy_k(int k, int nb, size_t n, const MultiPtr& X, const MultiCoef& c, void* y, cudaStream_t st) {
+template <int P>
+static void multi_axpy_k(int k, int nb, size_t nch, const MultiPtr& X, const MultiCoef& c, void* y, cudaStream_t st) {
     switch (k) {
-        case 1: k_multi_axpy<PX, PY, 1><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 2: k_multi_axpy<PX, PY, 2><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 3: k_multi_axpy<PX, PY, 3><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 4: k_multi_axpy<PX, PY, 4><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 5: k_multi_axpy<PX, PY, 5><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 6: k_multi_axpy<PX, PY, 6><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        case 7: k_multi_axpy<PX, PY, 7><<<nb, 256, 0, st>>>(n, X, c, y); break;
-        default: k_multi_axpy<PX, PY, 8><<<nb, 256, 0, st>>>(n, X, c, y); break;
+        case 1: k_multi_axpy<P, 1><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 2: k_multi_axpy<P, 2><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 3: k_multi_axpy<P, 3><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 4: k_multi_axpy<P, 4><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 5: k_multi_axpy<P, 5><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 6: k_multi_axpy<P, 6><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 7: k_multi_axpy<P, 7><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        default: k_multi_axpy<P, 8><<<nb, 256, 0, st>>>(nch, X, c, y); break;
     }
 }
 
 int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
                     const void* const* X, void* y, cudaStream_t st) {
-    const int nb = upd_blocks(ctx, n);
+    // the flat complex order is the same only within one precision
+    if (px != py) return qxd_fail(ctx, QXD_EARG, "blas_multi_axpy: precisions must match");
+    const size_t nc = nchunks(px, n);
+    const int nb = upd_blocks(ctx, nc);
     for (int j0 = 0; j0 < k; j0 += kMultiMax) {
         const int kk = (k - j0) < kMultiMax ? (k - j0) : kMultiMax;
         MultiPtr mp;
@@ -341,11 +428,9 @@ int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double*
             mc.im[j] = j < kk ? cim[jj] : 0.0;
         }
         ProfScope prof(ctx, "multi_axpy", (double)n * (eb(px) * kk + 2 * eb(py)), st);
-        // the flat complex order is the same only within one precision
-        if (px == 0 && py == 0) multi_axpy_k<0, 0>(kk, nb, n, mp, mc, y, st);
-        else if (px == 1 && py == 1) multi_axpy_k<1, 1>(kk, nb, n, mp, mc, y, st);
-        else if (px == 2 && py == 2) multi_axpy_k<2, 2>(kk, nb, n, mp, mc, y, st);
-        else return qxd_fail(ctx, QXD_EARG, "blas_multi_axpy: precisions must match");
+        if (px == 0) multi_axpy_k<0>(kk, nb, nc, mp, mc, y, st);
+        else if (px == 1) multi_axpy_k<1>(kk, nb, nc, mp, mc, y, st);
+        else multi_axpy_k<2>(kk, nb, nc, mp, mc, y, st);
         QXD_CUDA(ctx, cudaGetLastError());
     }
     return QXD_OK;
