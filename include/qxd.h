@@ -176,6 +176,30 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
 int qxd_solve_multishift(qxd_ctx* ctx, int fl, int nshift, const double* sigma, const qxd_solver* s,
                          const void* phi_e, void* x_e, qxd_info* info, void* stream);
 
+/* Dhat for callers that cannot allocate device memory during the call.  The
+ * paper has no counterpart; this is an interface convenience.  Some callers own
+ * all device memory through their own pool allocator and have nothing left for
+ * the library, and cudaMalloc synchronises the whole device, which a tight
+ * asynchronous loop cannot afford.  qxd_apply_Dhat_eo grows the context's
+ * workspace with cudaMalloc on first use.  This entry point computes the same
+ * out_e = Dhat in_e (dagger: Dhat^+), with the same kernels, for one
+ * right-hand side, and allocates nothing.  Its temporaries are held in one
+ * file-scope device array of 18 MiB.  Every GPU that loads the library holds
+ * that array until the process exits.
+ *  - Maximum size: V/2 <= 32768 even sites (e.g. 16^4, or 8x(2x8)x8x16 with C*);
+ *    larger lattices return QXD_EARG.
+ *  - in_e and out_e must be device arrays ([V/2][4][3] complex128 for QXD_FP64,
+ *    complex64 otherwise); host arrays return QXD_EARG (staging would allocate).
+ *  - The first call on a device looks up the array's device address with the
+ *    CUDA runtime.  Make that first call before any stream capture.
+ *  - Every call, from any context on the device, uses the same array.  Calls
+ *    whose work overlaps on the GPU (different streams, or different threads)
+ *    race and give wrong results.  Serialise them.  Each call overwrites the
+ *    whole array region it reads, so no state carries over between calls.
+ *  - Asynchronous on `stream`, like qxd_apply_Dhat_eo on device arrays. */
+int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dagger, const void* in_e, void* out_e,
+                              void* stream);
+
 /* Learned preconditioner weights for flavour fl (used by FGCR with
  * QXD_PRECOND_LEARNED).  The network M has nlayers gauge-covariant layers
  *   psi'_c(x) = sum_{c'} sum_{d=0..8} W[l][c][c'][d] T_d psi_{c'}(x),

@@ -24,7 +24,7 @@ STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: 
           5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
 
 EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_apply_Dw",
-           "qxd_apply_Dhat_eo", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
+           "qxd_apply_Dhat_eo", "qxd_apply_Dhat_eo_noalloc", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -75,6 +75,7 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_set_clover": (i, [vp, i, ctypes.POINTER(Flavour), vp]),
         "qxd_apply_Dw": (i, [vp, i, i, vp, vp, i, vp]),
         "qxd_apply_Dhat_eo": (i, [vp, i, i, i, vp, vp, i, vp]),
+        "qxd_apply_Dhat_eo_noalloc": (i, [vp, i, i, i, vp, vp, vp]),
         "qxd_solve": (i, [vp, i, ctypes.POINTER(Solver), vp, vp, i, ctypes.POINTER(Info), vp]),
         "qxd_solve_multishift": (i, [vp, i, i, vp, ctypes.POINTER(Solver), vp, vp, ctypes.POINTER(Info), vp]),
         "qxd_set_precond_weights": (i, [vp, i, vp, i, i]),
@@ -170,6 +171,11 @@ class Context:
     def apply_Dhat_eo(self, fl, prec, inp, out, dagger=False, nrhs=1, stream=None):
         self._check(self.lib.qxd_apply_Dhat_eo(self._h, int(fl), int(prec), int(bool(dagger)), _ptr(inp),
                                                _ptr(out), int(nrhs), _stream(stream)))
+
+    def apply_Dhat_eo_noalloc(self, fl, prec, inp, out, dagger=False, stream=None):
+        """Dhat without any device allocation (device arrays only, V/2 <= 32768)."""
+        self._check(self.lib.qxd_apply_Dhat_eo_noalloc(self._h, int(fl), int(prec), int(bool(dagger)), _ptr(inp),
+                                                       _ptr(out), _stream(stream)))
 
     def solve(self, fl, eta, psi, kind=FGCR, tol=1e-10, nmx=20000, nkv=16, inner=FP32, inner_tol=0.0,
               precond=PRECOND_NONE, nrhs=1, stream=None, check=True):
