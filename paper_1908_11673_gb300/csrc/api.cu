@@ -180,6 +180,8 @@ int qxd_create(const qxd_geom* g, int device, qxd_ctx** out) {
               cudaMalloc(&ctx->red_partials, kPartials * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&ctx->red_result, kRedSlots * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&ctx->dev_flag, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&ctx->red_ticket, sizeof(unsigned)) == cudaSuccess &&
+              cudaMemset(ctx->red_ticket, 0, sizeof(unsigned)) == cudaSuccess &&
               cudaMallocHost(&ctx->red_host, kRedSlots * sizeof(double)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -204,6 +206,7 @@ void qxd_destroy(qxd_ctx* ctx) {
     cudaFree(ctx->red_partials);
     cudaFree(ctx->red_result);
     cudaFree(ctx->dev_flag);
+    cudaFree(ctx->red_ticket);
     cudaFreeHost(ctx->red_host);
     delete ctx;
 }
@@ -361,8 +364,36 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
 int qxd_solve_multishift(qxd_ctx* ctx, int fl, int nshift, const double* sigma, const qxd_solver* s,
                          const void* phi_e, void* x_e, qxd_info* info, void* stream) {
     QXD_TRY(check_fl(ctx, fl));
-    (void)nshift; (void)sigma; (void)s; (void)phi_e; (void)x_e; (void)info; (void)stream;
-    return qxd_fail(ctx, QXD_ESTATE, "solve_multishift: not available in this build");
+    if (!s || !sigma || !phi_e || !x_e) return qxd_fail(ctx, QXD_EARG, "solve_multishift: NULL argument");
+    if (nshift < 1 || nshift > kMaxShifts) return qxd_fail(ctx, QXD_EARG, "solve_multishift: nshift must be 1..32");
+    for (int j = 0; j < nshift; ++j)
+        if (!(sigma[j] >= 0.0) || !std::isfinite(sigma[j]))
+            return qxd_fail(ctx, QXD_EARG, "solve_multishift: shifts must be finite and >= 0");
+    if (!(s->tol > 0.0) || s->nmx < 1) return qxd_fail(ctx, QXD_EARG, "solve_multishift: tol and nmx must be positive");
+    if (s->inner != QXD_FP64 && s->inner != QXD_FP32)
+        return qxd_fail(ctx, QXD_EARG, "solve_multishift: inner precision must be FP64 or FP32");
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cb = (size_t)ctx->g.Vh * 12 * 16;
+    const void* din;
+    void* dout;
+    bool host_out;
+    QXD_TRY(stage_in(ctx, WS_STAGE_IN, phi_e, cb, &din, st));
+    QXD_TRY(stage_out(ctx, WS_STAGE_OUT, x_e, cb * nshift, &dout, &host_out));
+    const size_t hb = half_bytes(ctx, QXD_FP64);
+    void *b64, *X64;
+    QXD_TRY(qxd_ws(ctx, WS_T8, hb, &b64));
+    QXD_TRY(qxd_ws(ctx, WS_T9, hb * nshift, &X64));
+    QXD_TRY(launch_pack(ctx, 0, din, 0, 0, QXD_FP64, b64, 1, st));
+    qxd_info local{};
+    int rc = solve_mscg(ctx, fl, nshift, sigma, s, b64, static_cast<char*>(X64), &local, st);
+    local.status = rc;
+    if (info) *info = local;
+    if (rc != QXD_OK && rc != QXD_ENOCONV) return rc;
+    QXD_TRY(launch_unpack(ctx, QXD_FP64, X64, 0, 0, dout, 0, nshift, st));
+    QXD_TRY(finish_out(ctx, x_e, dout, cb * nshift, host_out, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    return rc;
 }
 
 int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch) {

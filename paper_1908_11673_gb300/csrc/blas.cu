@@ -1,19 +1,27 @@
 // Vector kernels of the solvers: axpy-type updates, precision conversions and
-// deterministic reductions (block partial sums, then one block sums the
-// partials in a fixed order; every sum is accumulated in FP64).
+// deterministic reductions.
 //
 // Within one precision a field is handled as a flat array of n complex numbers
-// (the structure-of-arrays chunks store (re, im) pairs contiguously); operations
-// between two precisions go site by site through the layout-aware spinor access.
-#include "qxd_internal.h"
+// (the structure-of-arrays chunks store (re, im) pairs contiguously) and moved
+// in 16-byte chunks: one complex (FP64), two (FP32) or four (BF16) per chunk.
+// Arithmetic runs in the storage precision's real type (FP32 for FP32 and BF16
+// data; the FP64 pipe of this GPU runs at 1/64 of the FP32 rate); reductions
+// add FP32 partial sums of a few chunks into FP64 accumulators, and every sum
+// across threads and blocks is FP64.  Operations between two precisions go
+// site by site through the layout-aware spinor access, because the flat
+// complex order of the internal layout depends on the precision.
+//
+// A reduction is one launch: every block writes its partial sums, and the last
+// block to finish (a ticket counter) adds all partials in block order, so the
+// result is the same on every run.
+#include <map>
+#include <mutex>
+
 #include "blas.h"
+#include "qxd_internal.h"
 
 namespace qxd {
 
-// Flat access in 16-byte chunks: one complex (FP64), two (FP32) or four (BF16)
-// per chunk.  Arithmetic runs in the storage precision's real type (FP32 for
-// FP32 and BF16 data: the FP64 pipe of this GPU is 1/64 of the FP32 one);
-// reductions add FP32 partial sums of at most kFlush chunks into FP64 accumulators.
 template <int P> struct Chunk;
 template <> struct Chunk<0> {
     using R = double;
@@ -58,26 +66,65 @@ template <> struct Chunk<2> {
     }
 };
 
-constexpr int kFlush = 8;
-
+constexpr int kFlush = 8;        // chunks summed in FP32 before an FP64 flush
 constexpr int kRedThreads = 256;
-constexpr int kMaxRedBlocks = 1024;
+constexpr int kUnroll = 4;       // independent chunk loads in flight per thread
 
-static int red_blocks(size_t n) {
-    size_t b = (n + kRedThreads - 1) / kRedThreads;
-    return (int)(b < (size_t)kMaxRedBlocks ? (b > 0 ? b : 1) : kMaxRedBlocks);
+static size_t nchunks(int P, size_t n) { return n / (P == 0 ? 1 : (P == 1 ? 2 : 4)); }
+static double eb(int P) { return P == 0 ? 16.0 : (P == 1 ? 8.0 : 4.0); }
+
+// Grid of a grid-stride kernel: at most one full wave of resident blocks (the
+// occupancy of this kernel on this device, looked up once), and no more blocks
+// than the work needs.  A fixed grid for a given device and size keeps the
+// order of the reduction, and so its result, the same on every run.
+template <typename K>
+static int wave_blocks(qxd_ctx* ctx, K kernel, int threads, size_t work_per_block, size_t nch) {
+    static std::map<const void*, int> per_sm;  // per kernel instantiation
+    static std::mutex mu;
+    int b_sm;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = per_sm.find((const void*)kernel);
+        if (it == per_sm.end()) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess || n < 1) {
+                cudaGetLastError();
+                n = 1;
+            }
+            it = per_sm.emplace((const void*)kernel, n).first;
+        }
+        b_sm = it->second;
+    }
+    size_t cap = (size_t)b_sm * ctx->nsm;
+    if (cap > (size_t)kMaxRedBlocks) cap = kMaxRedBlocks;
+    size_t need = (nch + work_per_block - 1) / work_per_block;
+    return (int)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
-// sum of NC doubles over the block, written to partials[c * gridDim.x + blockIdx.x]
+static int upd_blocks(qxd_ctx* ctx, size_t n) {
+    size_t b = (n + 255) / 256;
+    size_t cap = (size_t)ctx->nsm * 16;
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+struct RedOut {
+    double* partials;
+    unsigned* ticket;
+    double* result;
+};
+
+static RedOut red_out(qxd_ctx* ctx, int slot) { return RedOut{ctx->red_partials, ctx->red_ticket, ctx->red_result + slot}; }
+
 template <int NC>
-__device__ void block_reduce_store(double v[NC], double* __restrict__ partials) {
+__device__ void block_reduce_finish(double v[NC], const RedOut& o) {
     __shared__ double sh[NC][kRedThreads / 32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         double x = v[c];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
         if (lane == 0) sh[c][warp] = x;
     }
     __syncthreads();
@@ -86,104 +133,99 @@ __device__ void block_reduce_store(double v[NC], double* __restrict__ partials) 
         for (int c = 0; c < NC; ++c) {
             double x = lane < kRedThreads / 32 ? sh[c][lane] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) partials[(size_t)c * gridDim.x + blockIdx.x] = x;
+            for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+            if (lane == 0) o.partials[(size_t)c * gridDim.x + blockIdx.x] = x;
         }
     }
-}
-
-// one block: result[c] = sum_b partials[c * nb + b], fixed order
-__global__ void k_final(const double* __restrict__ partials, int nb, int ncomp, double* __restrict__ result) {
-    __shared__ double sh[kRedThreads / 32];
-    for (int c = 0; c < ncomp; ++c) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(o.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nb = gridDim.x;
+    for (int c = 0; c < NC; ++c) {
         double x = 0.0;
-        for (int b = threadIdx.x; b < nb; b += blockDim.x) x += partials[(size_t)c * nb + b];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) x += __ldcg(o.partials + (size_t)c * nb + b);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) sh[warp] = x;
+        for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+        __syncthreads();
+        if (lane == 0) sh[0][warp] = x;
         __syncthreads();
         if (warp == 0) {
-            x = lane < kRedThreads / 32 ? sh[lane] : 0.0;
+            x = lane < kRedThreads / 32 ? sh[0][lane] : 0.0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) result[c] = x;
+            for (int s = 16; s > 0; s >>= 1) x += __shfl_down_sync(0xffffffffu, x, s);
+            if (lane == 0) o.result[c] = x;
         }
-        __syncthreads();
     }
+    if (threadIdx.x == 0) *o.ticket = 0u;
 }
 
-static double eb(int P) { return P == 0 ? 16.0 : (P == 1 ? 8.0 : 4.0); }
-
-static int finish(qxd_ctx* ctx, int nb, int ncomp, int slot, cudaStream_t st) {
-    QXD_CUDA(ctx, cudaGetLastError());
-    ProfScope prof(ctx, "reduce_final", 8.0 * nb * ncomp, st);
-    k_final<<<1, kRedThreads, 0, st>>>(ctx->red_partials, nb, ncomp, ctx->red_result + slot);
-    QXD_CUDA(ctx, cudaGetLastError());
-    return QXD_OK;
-}
-
-// ---- reductions ---------------------------------------------------------------
-// n counts complex numbers; every kernel walks over n / NC chunks.
+// ---- reductions -------------------------------------------------------------------
 template <int P>
 __global__ void __launch_bounds__(kRedThreads) k_dot(size_t nch, const void* __restrict__ a,
-                                                     const void* __restrict__ b, double* __restrict__ partials) {
+                                                     const void* __restrict__ b, RedOut o) {
     using R = typename Chunk<P>::R;
     constexpr int NC = Chunk<P>::NC;
     double v[2] = {0.0, 0.0};
-    R f[2] = {R(0), R(0)};
-    int cnt = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
-        cplx<R> x[NC], y[NC];
-        Chunk<P>::ld(a, i, x);
-        Chunk<P>::ld(b, i, y);
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < nch; i0 += S * kUnroll) {
+        cplx<R> x[kUnroll][NC], y[kUnroll][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            f[0] = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, f[0]));
-            f[1] = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, f[1]));
-        }
-        if (++cnt == kFlush) {
-            v[0] += f[0]; v[1] += f[1];
-            f[0] = f[1] = R(0);
-            cnt = 0;
-        }
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < nch) {
+                Chunk<P>::ld(a, i0 + u * S, x[u]);
+                Chunk<P>::ld(b, i0 + u * S, y[u]);
+            }
+        R f[2] = {R(0), R(0)};
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < nch) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    f[0] = fma(x[u][c].re, y[u][c].re, fma(x[u][c].im, y[u][c].im, f[0]));
+                    f[1] = fma(x[u][c].re, y[u][c].im, fma(-x[u][c].im, y[u][c].re, f[1]));
+                }
+            }
+        v[0] += f[0];
+        v[1] += f[1];
     }
-    v[0] += f[0];
-    v[1] += f[1];
-    block_reduce_store<2>(v, partials);
+    block_reduce_finish<2>(v, o);
 }
 
 template <int P>
-__global__ void __launch_bounds__(kRedThreads) k_norm2(size_t nch, const void* __restrict__ a,
-                                                       double* __restrict__ partials) {
+__global__ void __launch_bounds__(kRedThreads) k_norm2(size_t nch, const void* __restrict__ a, RedOut o) {
     using R = typename Chunk<P>::R;
     constexpr int NC = Chunk<P>::NC;
-    double v[2] = {0.0, 0.0};  // |a|^2 and a count of non-finite entries
-    R f = R(0);
-    int cnt = 0, bad = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
-        cplx<R> x[NC];
-        Chunk<P>::ld(a, i, x);
-        R s = R(0);
+    double v[2] = {0.0, 0.0};  // |a|^2 over finite chunks, count of non-finite chunks
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < nch; i0 += S * kUnroll) {
+        cplx<R> x[kUnroll][NC];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) s = fma(x[c].re, x[c].re, fma(x[c].im, x[c].im, s));
-        if (isfinite(s)) f += s;
-        else ++bad;
-        if (++cnt == kFlush) {
-            v[0] += f;
-            f = R(0);
-            cnt = 0;
-        }
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < nch) Chunk<P>::ld(a, i0 + u * S, x[u]);
+        R f = R(0);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < nch) {
+                R s = R(0);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) s = fma(x[u][c].re, x[u][c].re, fma(x[u][c].im, x[u][c].im, s));
+                if (isfinite(s)) f += s;
+                else v[1] += 1.0;
+            }
+        v[0] += f;
     }
-    v[0] += f;
-    v[1] = bad;
-    block_reduce_store<2>(v, partials);
+    block_reduce_finish<2>(v, o);
 }
 
-// k dot products <W_j, v>, j < k (k <= kMultiMax)
+// <W_j, v> for j < K
 template <int P, int K>
 __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr W, const void* __restrict__ v,
-                                                           double* __restrict__ partials) {
+                                                           RedOut o) {
     using R = typename Chunk<P>::R;
     constexpr int NC = Chunk<P>::NC;
     double acc[2 * K];
@@ -194,19 +236,20 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr 
         f[c] = R(0);
     }
     int cnt = 0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += S) {
         cplx<R> y[NC];
         Chunk<P>::ld(v, i, y);
+        cplx<R> x[K][NC];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            cplx<R> x[NC];
-            Chunk<P>::ld(W.p[j], i, x);
+        for (int j = 0; j < K; ++j) Chunk<P>::ld(W.p[j], i, x[j]);
+#pragma unroll
+        for (int j = 0; j < K; ++j)
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
-                f[2 * j] = fma(x[c].re, y[c].re, fma(x[c].im, y[c].im, f[2 * j]));
-                f[2 * j + 1] = fma(x[c].re, y[c].im, fma(-x[c].im, y[c].re, f[2 * j + 1]));
+                f[2 * j] = fma(x[j][c].re, y[c].re, fma(x[j][c].im, y[c].im, f[2 * j]));
+                f[2 * j + 1] = fma(x[j][c].re, y[c].im, fma(-x[j][c].im, y[c].re, f[2 * j + 1]));
             }
-        }
         if (++cnt == kFlush) {
 #pragma unroll
             for (int c = 0; c < 2 * K; ++c) {
@@ -218,72 +261,79 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr 
     }
 #pragma unroll
     for (int c = 0; c < 2 * K; ++c) acc[c] += f[c];
-    block_reduce_store<2 * K>(acc, partials);
+    block_reduce_finish<2 * K>(acc, o);
 }
 
-static size_t nchunks(int P, size_t n) { return n / (P == 0 ? 1 : (P == 1 ? 2 : 4)); }
-
 int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* b, int slot, cudaStream_t st) {
-    // the flat complex order is the same only within one precision
     if (pa != pb) return qxd_fail(ctx, QXD_EARG, "blas_dot: precisions must match");
     const size_t nc = nchunks(pa, n);
-    const int nb = red_blocks(nc);
-    {
-        ProfScope prof(ctx, "dot", (double)n * (eb(pa) + eb(pb)), st);
-        if (pa == 0) k_dot<0><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
-        else if (pa == 1) k_dot<1><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
-        else k_dot<2><<<nb, kRedThreads, 0, st>>>(nc, a, b, ctx->red_partials);
-    }
-    return finish(ctx, nb, 2, slot, st);
+    ProfScope prof(ctx, "dot", (double)n * 2 * eb(pa), st);
+    const RedOut o = red_out(ctx, slot);
+    const size_t wpb = (size_t)kRedThreads * kUnroll;
+#define QXD_LAUNCH(P) k_dot<P><<<wave_blocks(ctx, k_dot<P>, kRedThreads, wpb, nc), kRedThreads, 0, st>>>(nc, a, b, o)
+    if (pa == 0) QXD_LAUNCH(0);
+    else if (pa == 1) QXD_LAUNCH(1);
+    else QXD_LAUNCH(2);
+#undef QXD_LAUNCH
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
 }
 
 int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st) {
     const size_t nc = nchunks(p, n);
-    const int nb = red_blocks(nc);
-    {
-        ProfScope prof(ctx, "norm2", (double)n * eb(p), st);
-        if (p == 0) k_norm2<0><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
-        else if (p == 1) k_norm2<1><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
-        else k_norm2<2><<<nb, kRedThreads, 0, st>>>(nc, a, ctx->red_partials);
-    }
-    return finish(ctx, nb, 2, slot, st);
+    ProfScope prof(ctx, "norm2", (double)n * eb(p), st);
+    const RedOut o = red_out(ctx, slot);
+    const size_t wpb = (size_t)kRedThreads * kUnroll;
+#define QXD_LAUNCH(P) k_norm2<P><<<wave_blocks(ctx, k_norm2<P>, kRedThreads, wpb, nc), kRedThreads, 0, st>>>(nc, a, o)
+    if (p == 0) QXD_LAUNCH(0);
+    else if (p == 1) QXD_LAUNCH(1);
+    else QXD_LAUNCH(2);
+#undef QXD_LAUNCH
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+template <int P, int K>
+static void multi_dot_launch(qxd_ctx* ctx, size_t nch, const MultiPtr& W, const void* v, const RedOut& o,
+                             cudaStream_t st) {
+    const int nb = wave_blocks(ctx, k_multi_dot<P, K>, kRedThreads, (size_t)kRedThreads * 2, nch);
+    k_multi_dot<P, K><<<nb, kRedThreads, 0, st>>>(nch, W, v, o);
 }
 
 template <int P>
-static void multi_dot_k(int k, int nb, size_t n, const MultiPtr& W, const void* v, double* partials, cudaStream_t st) {
+static void multi_dot_k(qxd_ctx* ctx, int k, size_t nch, const MultiPtr& W, const void* v, const RedOut& o,
+                        cudaStream_t st) {
     switch (k) {
-        case 1: k_multi_dot<P, 1><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 2: k_multi_dot<P, 2><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 3: k_multi_dot<P, 3><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 4: k_multi_dot<P, 4><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 5: k_multi_dot<P, 5><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 6: k_multi_dot<P, 6><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        case 7: k_multi_dot<P, 7><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
-        default: k_multi_dot<P, 8><<<nb, kRedThreads, 0, st>>>(n, W, v, partials); break;
+        case 1: multi_dot_launch<P, 1>(ctx, nch, W, v, o, st); break;
+        case 2: multi_dot_launch<P, 2>(ctx, nch, W, v, o, st); break;
+        case 3: multi_dot_launch<P, 3>(ctx, nch, W, v, o, st); break;
+        case 4: multi_dot_launch<P, 4>(ctx, nch, W, v, o, st); break;
+        case 5: multi_dot_launch<P, 5>(ctx, nch, W, v, o, st); break;
+        case 6: multi_dot_launch<P, 6>(ctx, nch, W, v, o, st); break;
+        case 7: multi_dot_launch<P, 7>(ctx, nch, W, v, o, st); break;
+        default: multi_dot_launch<P, 8>(ctx, nch, W, v, o, st); break;
     }
 }
 
 int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, const void* v, int slot,
                    cudaStream_t st) {
+    const size_t nc = nchunks(p, n);
     for (int j0 = 0; j0 < k; j0 += kMultiMax) {
         const int kk = (k - j0) < kMultiMax ? (k - j0) : kMultiMax;
         MultiPtr mp;
         for (int j = 0; j < kMultiMax; ++j) mp.p[j] = W[j0 + (j < kk ? j : 0)];
-        const size_t nc = nchunks(p, n);
-        const int nb = red_blocks(nc);
-        {
         ProfScope prof(ctx, "multi_dot", (double)n * eb(p) * (kk + 1), st);
-        if (p == 0) multi_dot_k<0>(kk, nb, nc, mp, v, ctx->red_partials, st);
-        else if (p == 1) multi_dot_k<1>(kk, nb, nc, mp, v, ctx->red_partials, st);
-        else multi_dot_k<2>(kk, nb, nc, mp, v, ctx->red_partials, st);
-        }
-        QXD_TRY(finish(ctx, nb, 2 * kk, slot + 2 * j0, st));
+        const RedOut o = red_out(ctx, slot + 2 * j0);
+        if (p == 0) multi_dot_k<0>(ctx, kk, nc, mp, v, o, st);
+        else if (p == 1) multi_dot_k<1>(ctx, kk, nc, mp, v, o, st);
+        else multi_dot_k<2>(ctx, kk, nc, mp, v, o, st);
+        QXD_CUDA(ctx, cudaGetLastError());
     }
     return QXD_OK;
 }
 
-// ---- updates -------------------------------------------------------------------
-// y = a*x + b*y (same precision, arithmetic in its real type)
+// ---- updates --------------------------------------------------------------------
+// y = a*x + b*y (same precision)
 template <int P>
 __global__ void k_axpby(size_t nch, double ar, double ai, const void* __restrict__ x, double br, double bi,
                         void* __restrict__ y) {
@@ -305,9 +355,7 @@ __global__ void k_axpby(size_t nch, double ar, double ai, const void* __restrict
     }
 }
 
-// Mixed-precision y = a*x + b*y.  The flat complex order differs between the
-// precisions (one, two or four complex numbers per 16-byte chunk), so these
-// kernels walk over sites and use the layout-aware spinor load and store.
+// y = a*x + b*y between two precisions, site by site
 template <int PX, int PY>
 __global__ void k_axpby_site(int Vh, int nfields, double ar, double ai, const void* __restrict__ x, double br,
                              double bi, void* __restrict__ y) {
@@ -341,32 +389,46 @@ __global__ void k_axpby_site(int Vh, int nfields, double ar, double ai, const vo
     }
 }
 
-// y += sum_j c_j X_j  (k <= kMultiMax; same precision, arithmetic in its real type)
-template <int P, int K>
-__global__ void k_multi_axpy(size_t nch, MultiPtr X, MultiCoef c, void* __restrict__ y) {
+// y += sum_j c_j X_j (same precision); with NORM also |y|^2 of the result
+template <int P, int K, bool NORM>
+__global__ void __launch_bounds__(kRedThreads) k_multi_axpy(size_t nch, MultiPtr X, MultiCoef c,
+                                                            void* __restrict__ y, RedOut o) {
     using R = typename Chunk<P>::R;
     constexpr int NC = Chunk<P>::NC;
     cplx<R> cf[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) cf[j] = {(R)c.re[j], (R)c.im[j]};
+    double v[2] = {0.0, 0.0};
+    R f = R(0);
+    int cnt = 0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
         cplx<R> yv[NC];
         Chunk<P>::ld(y, i, yv);
+        cplx<R> xv[K][NC];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            cplx<R> xv[NC];
-            Chunk<P>::ld(X.p[j], i, xv);
+        for (int j = 0; j < K; ++j) Chunk<P>::ld(X.p[j], i, xv[j]);
 #pragma unroll
-            for (int q = 0; q < NC; ++q) cmac(yv[q], cf[j], xv[q]);
-        }
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int q = 0; q < NC; ++q) cmac(yv[q], cf[j], xv[j][q]);
         Chunk<P>::st(y, i, yv);
+        if (NORM) {
+            R s = R(0);
+#pragma unroll
+            for (int q = 0; q < NC; ++q) s = fma(yv[q].re, yv[q].re, fma(yv[q].im, yv[q].im, s));
+            if (isfinite(s)) f += s;
+            else v[1] += 1.0;
+            if (++cnt == kFlush) {
+                v[0] += f;
+                f = R(0);
+                cnt = 0;
+            }
+        }
     }
-}
-
-static int upd_blocks(qxd_ctx* ctx, size_t n) {
-    size_t b = (n + 255) / 256;
-    size_t cap = (size_t)ctx->nsm * 16;
-    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+    if (NORM) {
+        v[0] += f;
+        block_reduce_finish<2>(v, o);
+    }
 }
 
 int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, const void* x, double br, double bi,
@@ -397,28 +459,36 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
     return QXD_OK;
 }
 
-template <int P>
-static void multi_axpy_k(int k, int nb, size_t nch, const MultiPtr& X, const MultiCoef& c, void* y, cudaStream_t st) {
+template <int P, int K, bool NORM>
+static void multi_axpy_launch(qxd_ctx* ctx, size_t nch, const MultiPtr& X, const MultiCoef& c, void* y,
+                              const RedOut& o, cudaStream_t st) {
+    const int nb = NORM ? wave_blocks(ctx, k_multi_axpy<P, K, NORM>, kRedThreads, (size_t)kRedThreads * 2, nch)
+                        : upd_blocks(ctx, nch);
+    k_multi_axpy<P, K, NORM><<<nb, kRedThreads, 0, st>>>(nch, X, c, y, o);
+}
+
+template <int P, bool NORM>
+static void multi_axpy_k(qxd_ctx* ctx, int k, size_t nch, const MultiPtr& X, const MultiCoef& c, void* y,
+                         const RedOut& o, cudaStream_t st) {
     switch (k) {
-        case 1: k_multi_axpy<P, 1><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 2: k_multi_axpy<P, 2><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 3: k_multi_axpy<P, 3><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 4: k_multi_axpy<P, 4><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 5: k_multi_axpy<P, 5><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 6: k_multi_axpy<P, 6><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        case 7: k_multi_axpy<P, 7><<<nb, 256, 0, st>>>(nch, X, c, y); break;
-        default: k_multi_axpy<P, 8><<<nb, 256, 0, st>>>(nch, X, c, y); break;
+        case 1: multi_axpy_launch<P, 1, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 2: multi_axpy_launch<P, 2, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 3: multi_axpy_launch<P, 3, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 4: multi_axpy_launch<P, 4, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 5: multi_axpy_launch<P, 5, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 6: multi_axpy_launch<P, 6, NORM>(ctx, nch, X, c, y, o, st); break;
+        case 7: multi_axpy_launch<P, 7, NORM>(ctx, nch, X, c, y, o, st); break;
+        default: multi_axpy_launch<P, 8, NORM>(ctx, nch, X, c, y, o, st); break;
     }
 }
 
-int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
-                    const void* const* X, void* y, cudaStream_t st) {
-    // the flat complex order is the same only within one precision
+static int multi_axpy_impl(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
+                           const void* const* X, void* y, int norm_slot, cudaStream_t st) {
     if (px != py) return qxd_fail(ctx, QXD_EARG, "blas_multi_axpy: precisions must match");
     const size_t nc = nchunks(px, n);
-    const int nb = upd_blocks(ctx, nc);
     for (int j0 = 0; j0 < k; j0 += kMultiMax) {
         const int kk = (k - j0) < kMultiMax ? (k - j0) : kMultiMax;
+        const bool norm = norm_slot >= 0 && j0 + kk == k;  // the norm is taken after the last chunk
         MultiPtr mp;
         MultiCoef mc;
         for (int j = 0; j < kMultiMax; ++j) {
@@ -427,12 +497,71 @@ int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double*
             mc.re[j] = j < kk ? cre[jj] : 0.0;
             mc.im[j] = j < kk ? cim[jj] : 0.0;
         }
-        ProfScope prof(ctx, "multi_axpy", (double)n * (eb(px) * kk + 2 * eb(py)), st);
-        if (px == 0) multi_axpy_k<0>(kk, nb, nc, mp, mc, y, st);
-        else if (px == 1) multi_axpy_k<1>(kk, nb, nc, mp, mc, y, st);
-        else multi_axpy_k<2>(kk, nb, nc, mp, mc, y, st);
+        ProfScope prof(ctx, norm ? "multi_axpy_norm" : "multi_axpy", (double)n * (eb(px) * kk + 2 * eb(py)), st);
+        const RedOut o = red_out(ctx, norm ? norm_slot : 0);
+        if (norm) {
+            if (px == 0) multi_axpy_k<0, true>(ctx, kk, nc, mp, mc, y, o, st);
+            else if (px == 1) multi_axpy_k<1, true>(ctx, kk, nc, mp, mc, y, o, st);
+            else multi_axpy_k<2, true>(ctx, kk, nc, mp, mc, y, o, st);
+        } else {
+            if (px == 0) multi_axpy_k<0, false>(ctx, kk, nc, mp, mc, y, o, st);
+            else if (px == 1) multi_axpy_k<1, false>(ctx, kk, nc, mp, mc, y, o, st);
+            else multi_axpy_k<2, false>(ctx, kk, nc, mp, mc, y, o, st);
+        }
         QXD_CUDA(ctx, cudaGetLastError());
     }
+    return QXD_OK;
+}
+
+int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
+                    const void* const* X, void* y, cudaStream_t st) {
+    return multi_axpy_impl(ctx, px, py, n, k, cre, cim, X, y, -1, st);
+}
+
+int blas_multi_axpy_norm(qxd_ctx* ctx, int p, size_t n, int k, const double* cre, const double* cim,
+                         const void* const* X, void* y, int slot, cudaStream_t st) {
+    if (k < 1) return blas_norm2(ctx, p, n, y, slot, st);
+    return multi_axpy_impl(ctx, p, p, n, k, cre, cim, X, y, slot, st);
+}
+
+// ---- multi-shift CG update ---------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(256) k_msg_update(size_t nch, int ns, ShiftPtrs ptr, ShiftCoef c,
+                                                    const void* __restrict__ r) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> rv[NC];
+        Chunk<P>::ld(r, i, rv);
+        for (int j = 0; j < ns; ++j) {
+            cplx<R> xv[NC], pv[NC];
+            Chunk<P>::ld(ptr.x[j], i, xv);
+            Chunk<P>::ld(ptr.p[j], i, pv);
+            const R a = (R)c.alpha[j], z = (R)c.zeta[j], b = (R)c.beta[j];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                xv[q].re = fma(a, pv[q].re, xv[q].re);
+                xv[q].im = fma(a, pv[q].im, xv[q].im);
+                pv[q].re = fma(z, rv[q].re, b * pv[q].re);
+                pv[q].im = fma(z, rv[q].im, b * pv[q].im);
+            }
+            Chunk<P>::st(ptr.x[j], i, xv);
+            Chunk<P>::st(ptr.p[j], i, pv);
+        }
+    }
+}
+
+int blas_msg_update(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr, const ShiftCoef& c, const void* r,
+                    cudaStream_t st) {
+    if (ns < 1) return QXD_OK;
+    if (ns > kMaxShifts) return qxd_fail(ctx, QXD_EARG, "msg_update: too many shifts");
+    const size_t nc = nchunks(P, n);
+    const int nb = upd_blocks(ctx, nc);
+    ProfScope prof(ctx, "msg_update", (double)n * eb(P) * (1 + 4 * ns), st);
+    if (P == 0) k_msg_update<0><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    else if (P == 1) k_msg_update<1><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    else k_msg_update<2><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }
 

@@ -10,7 +10,8 @@ namespace qxd {
 
 constexpr int kMultiMax = 8;
 constexpr int kRedSlots = 512;
-constexpr int kPartials = 16 * 1024;
+constexpr int kMaxRedBlocks = 1024;
+constexpr int kPartials = 2 * kMultiMax * kMaxRedBlocks;
 
 struct MultiPtr {
     const void* p[kMultiMax];
@@ -37,6 +38,29 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
 // y += sum_j c_j X_j  (px == py)
 int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
                     const void* const* X, void* y, cudaStream_t st);
+// y += sum_j c_j X_j, then result[slot] = |y|^2, result[slot+1] = non-finite count
+int blas_multi_axpy_norm(qxd_ctx* ctx, int p, size_t n, int k, const double* cre, const double* cim,
+                         const void* const* X, void* y, int slot, cudaStream_t st);
 int blas_fetch(qxd_ctx* ctx, int nslots, cudaStream_t st);
+
+}  // namespace qxd
+
+namespace qxd {
+
+constexpr int kMaxShifts = 32;
+
+// Fused multi-shift CG update over the active shifts j < ns (one pass over r):
+//   x_j += alpha_j p_j;   p_j = zeta_j r + beta_j p_j
+struct ShiftPtrs {
+    void* x[kMaxShifts];
+    void* p[kMaxShifts];
+};
+struct ShiftCoef {
+    double alpha[kMaxShifts];
+    double zeta[kMaxShifts];
+    double beta[kMaxShifts];
+};
+int blas_msg_update(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr, const ShiftCoef& c, const void* r,
+                    cudaStream_t st);
 
 }  // namespace qxd

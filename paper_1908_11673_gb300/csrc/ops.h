@@ -29,6 +29,9 @@ int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z,
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                  cudaStream_t st);
+// multi-shift CG: b64 even FP64 field, X64 ns consecutive FP64 even fields (output)
+int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solver* s, const void* b64, char* X64,
+               qxd_info* info, cudaStream_t st);
 int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                   cudaStream_t st);
 

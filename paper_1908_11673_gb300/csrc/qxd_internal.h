@@ -39,6 +39,7 @@ struct qxd_ctx {
     std::vector<size_t> ws_size;
     double* red_partials = nullptr;  // reduction scratch (per-block partial sums)
     double* red_result = nullptr;    // reduction results (device)
+    unsigned* red_ticket = nullptr;  // last-block ticket of the reductions (0 between launches)
     double* red_host = nullptr;      // pinned host mirror of the results
     int* dev_flag = nullptr;         // device error flag (singular block, non-finite)
     int nsm = 0;

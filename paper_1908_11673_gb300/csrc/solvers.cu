@@ -141,8 +141,55 @@ int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, con
 // ---------------------------------------------------------------------------
 // Flexible GCR on Dhat in precision P (even-site vectors), right preconditioner M.
 // Solves Dhat e = b to |b - Dhat e| <= rtol |b|; e is overwritten.
+// CG on the normal equations in precision P, tracking s = b - Dhat e:
+// always convergent (Dhat^+ Dhat is positive definite), used when restarted
+// GCR stagnates (a spectrum that surrounds the origin).  e is overwritten.
+int cgnr_inner(qxd_ctx* ctx, int fl, int P, const void* b, void* e, int max_iter, double rtol, int* iters,
+               cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *sv, *z, *p, *w, *to;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 100, hb, &sv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 101, hb, &z));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 102, hb, &p));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 103, hb, &w));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 104, hb, &to));
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(sv, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(op_Dhat(ctx, fl, P, 1, sv, z, to, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(p, z, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_TRY(blas_norm2(ctx, P, n, z, 2, st));
+    QXD_TRY(blas_fetch(ctx, 4, st));
+    const double bn = std::sqrt(ctx->red_host[0]);
+    double zz = ctx->red_host[2];
+    *iters = 0;
+    while (*iters < max_iter && zz > 0.0) {
+        QXD_TRY(op_Dhat(ctx, fl, P, 0, p, w, to, st));
+        QXD_TRY(blas_norm2(ctx, P, n, w, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "CGNR"));
+        const double ww = ctx->red_host[0];
+        *iters += 1;
+        if (!(ww > 0.0)) break;
+        const double alpha = zz / ww;
+        QXD_TRY(blas_axpby(ctx, P, P, n, alpha, 0.0, p, 1.0, 0.0, e, st));
+        QXD_TRY(blas_axpby(ctx, P, P, n, -alpha, 0.0, w, 1.0, 0.0, sv, st));
+        QXD_TRY(op_Dhat(ctx, fl, P, 1, sv, z, to, st));
+        QXD_TRY(blas_norm2(ctx, P, n, sv, 0, st));
+        QXD_TRY(blas_norm2(ctx, P, n, z, 2, st));
+        QXD_TRY(blas_fetch(ctx, 4, st));
+        if (std::sqrt(ctx->red_host[0]) <= rtol * bn) break;
+        const double beta = ctx->red_host[2] / zz;
+        zz = ctx->red_host[2];
+        QXD_TRY(blas_axpby(ctx, P, P, n, 1.0, 0.0, z, beta, 0.0, p, st));
+    }
+    return QXD_OK;
+}
+
 int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, void* e, int max_iter,
-               double rtol, int* iters, cudaStream_t st) {
+               double rtol, int* iters, bool* stagnated, cudaStream_t st) {
+    *stagnated = false;
     const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
     const size_t n = 12ull * ctx->g.Vh;
     const size_t hb = half_bytes(ctx, P);
@@ -169,6 +216,7 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
     bool done = false;
     while (!done && *iters < max_iter) {
         int K = 0;
+        const double rr_cycle = rr;
         for (int k = 0; k < nkv; ++k) {
             QXD_TRY(apply_precond(ctx, fl, P, s->precond, r, Z[k], st));
             QXD_TRY(op_Dhat(ctx, fl, P, 0, Z[k], W[k], to, st));
@@ -185,11 +233,10 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             }
             // <w_k, r> = conj(<r, w_k>); r is orthogonal to the earlier w_j
             const double wr_re = ctx->red_host[2 * k], wr_im = -ctx->red_host[2 * k + 1];
-            if (k > 0) {
+            {
                 std::vector<const void*> Wp(W.begin(), W.begin() + k);
-                QXD_TRY(blas_multi_axpy(ctx, P, P, n, k, cre.data(), cim.data(), Wp.data(), W[k], st));
+                QXD_TRY(blas_multi_axpy_norm(ctx, P, n, k, cre.data(), cim.data(), Wp.data(), W[k], 0, st));
             }
-            QXD_TRY(blas_norm2(ctx, P, n, W[k], 0, st));
             QXD_TRY(blas_fetch(ctx, 2, st));
             ww[k] = ctx->red_host[0];
             if (verbose())
@@ -230,6 +277,11 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             QXD_TRY(blas_fetch(ctx, 2, st));
             rr = ctx->red_host[0];
             if (rr <= rtol * rtol * bn * bn) done = true;
+            // a whole cycle that removed less than 10% of the residual norm
+            if (!done && K == nkv && rr > 0.81 * rr_cycle) {
+                *stagnated = true;
+                return QXD_OK;
+            }
         }
     }
     return QXD_OK;
@@ -271,6 +323,7 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb64, cudaMemcpyDeviceToDevice, st));
     QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb64, cudaMemcpyDeviceToDevice, st));
     double relres = 1.0;
+    bool use_cgnr = false;
     const double itol = s->inner_tol > 0 ? s->inner_tol : (P == QXD_BF16 ? 5e-3 : (P == QXD_FP32 ? 1e-5 : 1e-10));
     for (int outer = 0; outer < 64; ++outer) {
         if (outer > 0) {
@@ -290,9 +343,23 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         QXD_TRY(op_eo_source(ctx, fl, P, Full{tP, roP}, bP, to2, st));
         int it = 0;
         const double rtol = std::max(itol, 0.5 * s->tol / relres);
-        QXD_TRY(fgcr_inner(ctx, fl, P, s, bP, eeP, s->nmx - info->iters, rtol, &it, st));
-        info->iters += it;
-        info->op_applies += it + 2;
+        if (!use_cgnr) {
+            bool stag = false;
+            QXD_TRY(fgcr_inner(ctx, fl, P, s, bP, eeP, s->nmx - info->iters, rtol, &it, &stag, st));
+            info->iters += it;
+            info->op_applies += it + 2;
+            if (stag) {
+                // restarted GCR stalls on this operator: from here on the inner
+                // solves run CG on the normal equations, starting again from 0
+                use_cgnr = true;
+                if (verbose()) std::fprintf(stderr, "[qxd dc] GCR stagnated after %d iterations: CGNR inner\n", it);
+            }
+        }
+        if (use_cgnr) {
+            QXD_TRY(cgnr_inner(ctx, fl, P, bP, eeP, s->nmx - info->iters, rtol, &it, st));
+            info->iters += it;
+            info->op_applies += 2 * it + 1;
+        }
         // e_o = A_oo^-1 (r_o - H_oe e_e);  x += e
         QXD_TRY(op_odd_reconstruct(ctx, fl, P, roP, eeP, eoP, st));
         QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
@@ -303,6 +370,215 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     info->true_relres = std::sqrt(rr) / enorm;
     if (info->true_relres <= s->tol) return QXD_OK;
     return qxd_fail(ctx, QXD_ENOCONV, "FGCR: tolerance not reached within nmx");
+}
+
+}  // namespace qxd
+
+namespace qxd {
+
+// out = (Dhat^+ Dhat + sigma) v in precision P (tmp_e, tmp_o scratch)
+static int op_normal(qxd_ctx* ctx, int fl, int P, double sigma, const void* v, void* out, void* tmp_e, void* tmp_o,
+                     cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    QXD_TRY(op_Dhat(ctx, fl, P, 0, v, tmp_e, tmp_o, st));
+    QXD_TRY(op_Dhat(ctx, fl, P, 1, tmp_e, out, tmp_o, st));
+    if (sigma != 0.0) QXD_TRY(blas_axpby(ctx, P, P, n, sigma, 0.0, v, 1.0, 0.0, out, st));
+    return QXD_OK;
+}
+
+// CG on (Dhat^+ Dhat + sigma) e = b in precision P; e overwritten; stops at
+// |b - (A + sigma) e| <= rtol |b| (recursive residual).
+static int cg_shifted(qxd_ctx* ctx, int fl, int P, double sigma, const void* b, void* e, int max_iter, double rtol,
+                      int* iters, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *r, *p, *Ap, *te, *to;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 115, hb, &r));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 116, hb, &p));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 117, hb, &Ap));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 118, hb, &te));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 119, hb, &to));
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(p, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_TRY(blas_fetch(ctx, 2, st));
+    const double bn = std::sqrt(ctx->red_host[0]);
+    double rr = ctx->red_host[0];
+    *iters = 0;
+    if (bn == 0.0) return QXD_OK;
+    const double mone = -1.0;
+    while (*iters < max_iter) {
+        QXD_TRY(op_normal(ctx, fl, P, sigma, p, Ap, te, to, st));
+        QXD_TRY(blas_dot(ctx, P, P, n, p, Ap, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        const double pAp = ctx->red_host[0];
+        *iters += 1;
+        if (!(pAp > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "shifted CG: <p, A p> <= 0");
+        const double alpha = rr / pAp;
+        QXD_TRY(blas_axpby(ctx, P, P, n, alpha, 0.0, p, 1.0, 0.0, e, st));
+        const double ca = -alpha, ci = 0.0;
+        const void* Xp[1] = {Ap};
+        QXD_TRY(blas_multi_axpy_norm(ctx, P, n, 1, &ca, &ci, Xp, r, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "shifted CG"));
+        const double rr_new = ctx->red_host[0];
+        if (std::sqrt(rr_new) <= rtol * bn) break;
+        QXD_TRY(blas_axpby(ctx, P, P, n, 1.0, 0.0, r, rr_new / rr, 0.0, p, st));
+        rr = rr_new;
+    }
+    (void)mone;
+    return QXD_OK;
+}
+
+// Multi-shift CG in precision P on (Dhat^+ Dhat + sigma_j) x_j = b (Jegerlehner's
+// recursion: one Krylov space built with the smallest shift, the others
+// following through the scalars zeta_j).  X: ns fields of precision P (output).
+static int mscg_core(qxd_ctx* ctx, int fl, int P, int ns, const double* sigma, const void* b, char* X, int max_iter,
+                     double tol, int* iters, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *r, *pb, *Ap, *te, *to, *Pblk;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 110, hb, &r));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 111, hb, &pb));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 112, hb, &Ap));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 113, hb, &te));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 114, hb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 109, hb * ns, &Pblk));
+    char* Pc = static_cast<char*>(Pblk);
+    QXD_CUDA(ctx, cudaMemsetAsync(X, 0, hb * ns, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(pb, b, hb, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < ns; ++j) QXD_CUDA(ctx, cudaMemcpyAsync(Pc + j * hb, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_TRY(blas_fetch(ctx, 2, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "MSCG source"));
+    double rr = ctx->red_host[0];
+    const double bn = std::sqrt(rr);
+    *iters = 0;
+    if (bn == 0.0) return QXD_OK;
+    double s0 = sigma[0];
+    for (int j = 1; j < ns; ++j) s0 = std::min(s0, sigma[j]);
+    std::vector<double> zp(ns, 1.0), z(ns, 1.0), zn(ns, 1.0);
+    std::vector<char> active(ns, 1);
+    double alpha_prev = 1.0, beta_prev = 0.0;
+    while (*iters < max_iter) {
+        QXD_TRY(op_normal(ctx, fl, P, s0, pb, Ap, te, to, st));
+        QXD_TRY(blas_dot(ctx, P, P, n, pb, Ap, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        const double pAp = ctx->red_host[0];
+        *iters += 1;
+        if (!(pAp > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "MSCG: <p, A p> <= 0");
+        const double alpha = rr / pAp;
+        // r -= alpha A p, |r|^2
+        const double ca = -alpha, ci = 0.0;
+        const void* Xp[1] = {Ap};
+        QXD_TRY(blas_multi_axpy_norm(ctx, P, n, 1, &ca, &ci, Xp, r, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "MSCG"));
+        const double rr_new = ctx->red_host[0];
+        const double beta = rr_new / rr;
+        ShiftPtrs sp;
+        ShiftCoef sc;
+        int na = 0;
+        for (int j = 0; j < ns; ++j) {
+            if (!active[j]) continue;
+            const double ds = sigma[j] - s0;
+            const double den = alpha * beta_prev * (zp[j] - z[j]) + zp[j] * alpha_prev * (1.0 + ds * alpha);
+            zn[j] = z[j] * zp[j] * alpha_prev / den;
+            sp.x[na] = X + j * hb;
+            sp.p[na] = Pc + j * hb;
+            sc.alpha[na] = alpha * zn[j] / z[j];
+            sc.zeta[na] = zn[j];
+            sc.beta[na] = beta * (zn[j] / z[j]) * (zn[j] / z[j]);
+            ++na;
+        }
+        QXD_TRY(blas_msg_update(ctx, P, n, na, sp, sc, r, st));
+        QXD_TRY(blas_axpby(ctx, P, P, n, 1.0, 0.0, r, beta, 0.0, pb, st));
+        bool any = false;
+        for (int j = 0; j < ns; ++j) {
+            if (!active[j]) continue;
+            if (std::fabs(zn[j]) * std::sqrt(rr_new) <= tol * bn) active[j] = 0;
+            zp[j] = z[j];
+            z[j] = zn[j];
+            any = any || active[j];
+        }
+        if (verbose() && (*iters % 50 == 0))
+            std::fprintf(stderr, "[qxd mscg] it %d |r|/|b| %.3e\n", *iters, std::sqrt(rr_new) / bn);
+        rr = rr_new;
+        alpha_prev = alpha;
+        beta_prev = beta;
+        if (!any) return QXD_OK;
+    }
+    return QXD_OK;
+}
+
+int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solver* s, const void* b64, char* X64,
+               qxd_info* info, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb64 = half_bytes(ctx, QXD_FP64);
+    const int P = s->inner == QXD_FP64 ? QXD_FP64 : QXD_FP32;
+    info->iters = 0;
+    info->restarts = 0;
+    int it = 0;
+    QXD_TRY(blas_norm2(ctx, 0, n, b64, 0, st));
+    QXD_TRY(blas_fetch(ctx, 2, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "source"));
+    const double bn = std::sqrt(ctx->red_host[0]);
+    if (bn == 0.0) {
+        QXD_CUDA(ctx, cudaMemsetAsync(X64, 0, hb64 * ns, st));
+        info->true_relres = 0.0;
+        return QXD_OK;
+    }
+    if (P == QXD_FP64) {
+        QXD_TRY(mscg_core(ctx, fl, 0, ns, sigma, b64, X64, s->nmx, 0.5 * s->tol, &it, st));
+        info->iters += it;
+    } else {
+        const size_t hbP = half_bytes(ctx, P);
+        void *bP, *XP;
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 107, hbP, &bP));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 108, hbP * ns, &XP));
+        QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, b64, 0.0, 0.0, bP, st));
+        QXD_TRY(mscg_core(ctx, fl, P, ns, sigma, bP, static_cast<char*>(XP), s->nmx, std::max(s->tol, 1e-6), &it, st));
+        info->iters += it;
+        for (int j = 0; j < ns; ++j)
+            QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, static_cast<char*>(XP) + j * hbP, 0.0, 0.0, X64 + j * hb64, st));
+    }
+    // FP64 residual of every shift; FP32 defect correction where it misses tol
+    void *r64, *te, *to, *eP, *rP;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 104, hb64, &r64));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 105, hb64, &te));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 106, hb64, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 120, half_bytes(ctx, QXD_FP32), &eP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 121, half_bytes(ctx, QXD_FP32), &rP));
+    double worst = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        char* xj = X64 + j * hb64;
+        for (int pass = 0; pass < 16; ++pass) {
+            QXD_TRY(op_normal(ctx, fl, 0, sigma[j], xj, r64, te, to, st));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, b64, -1.0, 0.0, r64, st));
+            QXD_TRY(blas_norm2(ctx, 0, n, r64, 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "MSCG residual"));
+            const double rel = std::sqrt(ctx->red_host[0]) / bn;
+            if (verbose()) std::fprintf(stderr, "[qxd mscg] shift %d pass %d relres %.3e\n", j, pass, rel);
+            if (rel <= s->tol || info->iters >= s->nmx) {
+                worst = std::max(worst, rel);
+                break;
+            }
+            info->restarts += 1;
+            QXD_TRY(blas_axpby(ctx, 0, 1, n, 1.0, 0.0, r64, 0.0, 0.0, rP, st));
+            int ci = 0;
+            QXD_TRY(cg_shifted(ctx, fl, 1, sigma[j], rP, eP, s->nmx - info->iters, std::max(1e-5, 0.5 * s->tol / rel),
+                               &ci, st));
+            info->iters += ci;
+            QXD_TRY(blas_axpby(ctx, 1, 0, n, 1.0, 0.0, eP, 1.0, 0.0, xj, st));
+            if (pass == 15) worst = std::max(worst, rel);
+        }
+    }
+    info->true_relres = worst;
+    if (worst <= s->tol) return QXD_OK;
+    return qxd_fail(ctx, QXD_ENOCONV, "MSCG: tolerance not reached within nmx");
 }
 
 }  // namespace qxd
