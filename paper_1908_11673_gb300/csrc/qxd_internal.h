@@ -5,6 +5,7 @@
 
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/qxd.h"
@@ -59,6 +60,9 @@ struct qxd_ctx {
     std::map<std::string, int> prof_idx;
     std::vector<ProfPending> prof_pending;
     std::vector<cudaEvent_t> prof_pool;
+    // autotuned (rhs per thread, threads per block) of the multi-RHS hopping kernel,
+    // keyed by (precision, self mode, post mode, nrhs, V/2)
+    std::map<std::tuple<int, int, int, int, long long>, std::pair<int, int>> tune_hop;
 };
 
 // Brackets one kernel launch when profiling is on: counts it under `name` with
