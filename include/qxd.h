@@ -210,6 +210,41 @@ int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dagger, const 
  * other.  The network is not part of the paper. */
 int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch);
 
+/* ---- learned preconditioner: inference and training (not part of the paper) ----
+ * The network M and its weight layout are those of qxd_set_precond_weights.
+ * Even-site fields below are complex64 [V/2][4][3] in the canonical order;
+ * every array may be host or device memory. */
+
+/* out_e = (M in_e)_e: the network applied to in_e embedded in the full lattice
+ * (zero on odd sites), restricted to the even sites.  Synchronises `stream`. */
+int qxd_ptc_apply(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* in_e, void* out_e,
+                  void* stream);
+
+/* Loss L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2 over npairs pairs (r, e:
+ * [npairs][V/2][4][3] complex64) into *loss, and, if grad != NULL, its gradient
+ * G = dL/dW^* (Wirtinger; the gradient with respect to the real and imaginary
+ * parts of W is 2 Re G, 2 Im G), complex float32 in the layout of W. */
+int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* r, const void* e,
+                      int npairs, double* loss, float* grad, void* stream);
+
+/* nsteps steps of Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
+ * loss above, each over `batch` pairs taken in turn from the npairs given.  W is
+ * updated in place; m, v are the Adam moments (same size as W, zero at the
+ * start of training) and *t the step counter, all carried between calls so
+ * that training can alternate gauge fields (one context per field).
+ * losses (may be NULL) receives the mean loss of each step. */
+int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayers, int nch, const void* r,
+                  const void* e, int npairs, int batch, int nsteps, double lr, int* t, double* losses, void* stream);
+
+/* Training pairs from the plain FP64 solver: CG on the normal equations of
+ * Dhat x = b (b: complex128 [V/2][4][3]) run to |b - Dhat x| <= 1e-10 |b|; at
+ * iterations k = stride, 2 stride, ... the pair r = b - Dhat x_k, e = x* - x_k is
+ * recorded (x* the converged solution), npairs pairs into r_out, e_out
+ * (complex64 [npairs][V/2][4][3]).  QXD_ENOCONV if the solve does not
+ * converge, QXD_EARG if it converges before npairs * stride iterations. */
+int qxd_ptc_record_pairs(qxd_ctx* ctx, int fl, const void* b, int npairs, int stride, void* r_out, void* e_out,
+                         void* stream);
+
 /* Kernel profiling for benchmarks (not part of the paper).  mode 0: off;
  * 1: count the library's kernel launches by class; 2: also time each launch with
  * a CUDA event pair recorded on its launching stream.  Every call resets the

@@ -396,12 +396,6 @@ int qxd_solve_multishift(qxd_ctx* ctx, int fl, int nshift, const double* sigma, 
     return rc;
 }
 
-int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch) {
-    if (!ctx) return QXD_EARG;
-    (void)fl; (void)W; (void)nlayers; (void)nch;
-    return qxd_fail(ctx, QXD_ESTATE, "set_precond_weights: not available in this build");
-}
-
 int qxd_profile(qxd_ctx* ctx, int mode) {
     if (!ctx) return QXD_EARG;
     if (mode < 0 || mode > 2) return qxd_fail(ctx, QXD_EARG, "profile: mode must be 0, 1 or 2");

@@ -1,6 +1,7 @@
 // Operator compositions (Sec. 2.2): D, Dhat = D_ee - D_eo D_oo^-1 D_oe, the
 // even-odd source and the odd-site reconstruction, each as one or two launches
 // of the hopping kernel with a fused site-diagonal prologue or epilogue.
+#include "blas.h"
 #include "ops.h"
 
 namespace qxd {
@@ -84,12 +85,25 @@ int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void*
 }
 
 int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z, cudaStream_t st) {
-    (void)fl;
     if (kind == QXD_PRECOND_NONE) {
         QXD_CUDA(ctx, cudaMemcpyAsync(z, r, half_bytes(ctx, P), cudaMemcpyDeviceToDevice, st));
         return QXD_OK;
     }
-    return qxd_fail(ctx, QXD_EARG, "preconditioner kind not available");
+    if (kind == QXD_PRECOND_LEARNED) {
+        const QxdFlavour& F = ctx->fl[fl];
+        if (!F.W) return qxd_fail(ctx, QXD_ESTATE, "learned preconditioner weights not set");
+        const float2* W = reinterpret_cast<const float2*>(F.W);
+        if (P == QXD_FP32) return ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r, z, st);
+        // other precisions go through FP32 copies
+        void *r32, *z32;
+        const size_t n = 12ull * ctx->g.Vh;
+        QXD_TRY(qxd_ws(ctx, WS_PTC + 50, half_bytes(ctx, QXD_FP32), &r32));
+        QXD_TRY(qxd_ws(ctx, WS_PTC + 51, half_bytes(ctx, QXD_FP32), &z32));
+        QXD_TRY(blas_axpby(ctx, P, QXD_FP32, n, 1.0, 0.0, r, 0.0, 0.0, r32, st));
+        QXD_TRY(ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r32, z32, st));
+        return blas_axpby(ctx, QXD_FP32, P, n, 1.0, 0.0, z32, 0.0, 0.0, z, st);
+    }
+    return qxd_fail(ctx, QXD_EARG, "unknown preconditioner kind");
 }
 
 }  // namespace qxd

@@ -26,6 +26,10 @@ int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void*
 // z = M r (identity or the learned preconditioner)
 int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z, cudaStream_t st);
 
+// learned preconditioner (ptc.cu): z_e = (M r_e)_e on FP32 internal even fields
+int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const void* r_e, void* z_e,
+                       cudaStream_t st);
+
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                  cudaStream_t st);

@@ -1,0 +1,592 @@
+// Learned preconditioner: a gauge-covariant network of parallel-transport
+// layers (not part of the paper), with its training kernels.
+//
+// Layer l:  b_c(x) = sum_{c'} sum_{d=0..8} W[c][c'][d] (T_d a_{c'})(x)
+//   T_0 a(x) = a(x),  T_{1+mu} a(x) = V(x,mu) a(x+mu),  T_{5+mu} a(x) = V(x-mu,mu)^+ a(x-mu)
+// with V = U z^qhat and the boundary conditions of the Dirac operator (the
+// FP32 links and phases the hopping kernels use), W[c][c'][d] a complex 4x4
+// spin matrix.  Channels 1 -> nch -> ... -> nch -> 1.  As a preconditioner of
+// Dhat the network acts on an even-site field embedded in the full lattice and
+// its output is restricted to the even sites.
+//
+// Layout: a channel is a full-lattice FP32 field, the even then the odd
+// half-lattice field (6 float4 chunks x V/2 each); weights are complex (float2)
+// [cout][cin][9][4][4] per layer, layers one after the other.
+//
+// Training: loss L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2 over a batch of pairs;
+// gradient G = dL/dW^* = sum_x delta_c(x) (T_d a_{c'}(x))^+ (colour summed),
+// delta propagated backwards through the adjoint layers (W^+ and T_d^+ =
+// T_{opposite d}); Adam on the real and imaginary parts (gradient 2 Re G, 2 Im G).
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "blas.h"
+#include "hop.cuh"
+#include "ops.h"
+#include "qxd_internal.h"
+
+namespace qxd {
+
+constexpr int kPtcMaxCh = 16;
+constexpr int kPtcThreads = 128;
+
+struct PtcLinks {
+    const float4* U32;  // [p][12][Vh]
+    const float4* Z32;  // [p][2][Vh]
+};
+
+static size_t layer_weights(int cin, int cout) { return (size_t)cout * cin * 9 * 16; }  // complex entries
+
+static void layer_shape(int l, int nlayers, int nch, int* cin, int* cout) {
+    *cin = l == 0 ? 1 : nch;
+    *cout = l == nlayers - 1 ? 1 : nch;
+}
+
+size_t ptc_weight_count(int nlayers, int nch) {
+    size_t n = 0;
+    for (int l = 0; l < nlayers; ++l) {
+        int ci, co;
+        layer_shape(l, nlayers, nch, &ci, &co);
+        n += layer_weights(ci, co);
+    }
+    return n;
+}
+
+// (T_d a)(x) for the site (p, h) with coordinates x: the source site and the link
+QXD_HD void transport(const Geo& g, const PtcLinks& L, int d, int p, int h, const int x[4],
+                      const float4* __restrict__ a_ch, cplx<float> t[12]) {
+    const int Vh = g.Vh;
+    if (d == 0) {
+        load_spinor<1>(a_ch + (size_t)p * 6 * Vh, Vh, h, t);
+        return;
+    }
+    const int mu = (d - 1) & 3;
+    const bool fwd = d <= 4;
+    const int src = neighbour_lex(g, x, mu, fwd ? +1 : -1) >> 1;
+    const int ps = 1 - p;
+    cplx<float> s[12];
+    load_spinor<1>(a_ch + (size_t)ps * 6 * Vh, Vh, src, s);
+    Mat3<float> m;
+    cplx<float> z;
+    if (fwd) load_link32(L.U32 + (size_t)p * 12 * Vh, L.Z32 + (size_t)p * 2 * Vh, Vh, mu, h, m, z);
+    else load_link32(L.U32 + (size_t)ps * 12 * Vh, L.Z32 + (size_t)ps * 2 * Vh, Vh, mu, src, m, z);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (fwd) cmac(acc, m.a[i][j], s[3 * sp + j]);
+                else cmac_conj(acc, m.a[j][i], s[3 * sp + j]);
+            }
+            t[3 * sp + i] = fwd ? z * acc : cmul_conj(z, acc);
+        }
+}
+
+// one thread per (site, output channel); grid (sites/threads, 2 parities, cout)
+__global__ void __launch_bounds__(kPtcThreads) k_ptc_layer(Geo g, PtcLinks L, const float4* __restrict__ a, int cin,
+                                                           const float2* __restrict__ W, float4* __restrict__ out) {
+    extern __shared__ float2 wsh[];  // this output channel's weights [cin][9][4][4]
+    const int c = blockIdx.z;
+    const int nw = cin * 9 * 16;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) wsh[i] = W[(size_t)c * nw + i];
+    __syncthreads();
+    const int p = blockIdx.y;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= g.Vh) return;
+    const size_t chs = (size_t)12 * g.Vh;  // float4 per channel
+    int x[4];
+    site_coords(g, p, h, x);
+    cplx<float> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+    for (int d = 0; d < 9; ++d) {
+        for (int cp = 0; cp < cin; ++cp) {
+            cplx<float> t[12];
+            transport(g, L, d, p, h, x, a + cp * chs, t);
+            const float2* w = wsh + (cp * 9 + d) * 16;
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int sp = 0; sp < 4; ++sp) {
+                    const cplx<float> wv = {w[4 * s + sp].x, w[4 * s + sp].y};
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) cmac(acc[3 * s + i], wv, t[3 * sp + i]);
+                }
+        }
+    }
+    store_spinor<1>(out + c * chs + (size_t)p * 6 * g.Vh, g.Vh, h, acc);
+}
+
+// W'[c'][c][d'] = W[c][c'][opposite(d')]^+ (the adjoint layer as a forward layer)
+__global__ void k_ptc_adjoint_weights(const float2* __restrict__ W, int cin, int cout, float2* __restrict__ Wa) {
+    const int n = cout * cin * 9;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const int d = q % 9, cp = (q / 9) % cin, c = q / (9 * cin);
+        const int dop = d == 0 ? 0 : (d <= 4 ? d + 4 : d - 4);
+        const float2* src = W + ((size_t)(c * cin + cp) * 9 + d) * 16;
+        float2* dst = Wa + ((size_t)(cp * cout + c) * 9 + dop) * 16;
+        for (int s = 0; s < 4; ++s)
+            for (int t = 0; t < 4; ++t) dst[4 * t + s] = make_float2(src[4 * s + t].x, -src[4 * s + t].y);
+    }
+}
+
+// partial weight gradients: block (site chunk, triple q = (c*cin + c')*9 + d)
+constexpr int kWgBlocks = 32;
+__global__ void __launch_bounds__(kPtcThreads) k_ptc_wgrad(Geo g, PtcLinks L, const float4* __restrict__ delta,
+                                                           const float4* __restrict__ a, int cin,
+                                                           double* __restrict__ partials) {
+    const int q = blockIdx.y;
+    const int d = q % 9, cp = (q / 9) % cin, c = q / (9 * cin);
+    const size_t chs = (size_t)12 * g.Vh;
+    float f[32];
+    double acc[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        f[k] = 0.f;
+        acc[k] = 0.0;
+    }
+    int cnt = 0;
+    const int nsite = 2 * g.Vh;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsite; t += gridDim.x * blockDim.x) {
+        const int p = t / g.Vh, h = t % g.Vh;
+        int x[4];
+        site_coords(g, p, h, x);
+        cplx<float> s[12], dl[12];
+        transport(g, L, d, p, h, x, a + cp * chs, s);
+        load_spinor<1>(delta + c * chs + (size_t)p * 6 * g.Vh, g.Vh, h, dl);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cplx<float> v = {0.f, 0.f};
+#pragma unroll
+                for (int col = 0; col < 3; ++col) cmac_conj(v, s[3 * j + col], dl[3 * i + col]);
+                // v = sum_col conj(s[j][col]) delta[i][col] = (delta s^+)_{ij}
+                f[2 * (4 * i + j)] += v.re;
+                f[2 * (4 * i + j) + 1] += v.im;
+            }
+        if (++cnt == 16) {
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+                acc[k] += f[k];
+                f[k] = 0.f;
+            }
+            cnt = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] += f[k];
+    __shared__ double sh[32][kPtcThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int w = 0; w < kPtcThreads / 32; ++w) v += sh[threadIdx.x][w];
+        partials[((size_t)q * gridDim.x + blockIdx.x) * 32 + threadIdx.x] = v;
+    }
+}
+
+// G[q] (+)= sum over blocks of partials, fixed order; complex float output
+__global__ void k_ptc_wgrad_final(const double* __restrict__ partials, int nq, int nb, float2* __restrict__ G,
+                                  int accumulate) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq * 16; t += gridDim.x * blockDim.x) {
+        const int q = t / 16, e = t % 16;
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            re += partials[((size_t)q * nb + b) * 32 + 2 * e];
+            im += partials[((size_t)q * nb + b) * 32 + 2 * e + 1];
+        }
+        float2 g0 = accumulate ? G[t] : make_float2(0.f, 0.f);
+        G[t] = make_float2(g0.x + (float)re, g0.y + (float)im);
+    }
+}
+
+// Adam on the real view of W: gradient = scale * 2 (Re G, Im G)
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ G, float* __restrict__ m, float* __restrict__ v,
+                       size_t n, float scale, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gr = 2.f * scale * G[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gr;
+        const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ---- host side -------------------------------------------------------------------
+static PtcLinks links_of(qxd_ctx* ctx, int fl) { return PtcLinks{ctx->U32, ctx->fl[fl].Z32}; }
+
+static size_t chan_bytes(const qxd_ctx* ctx) { return (size_t)ctx->g.Vh * 2 * 96; }
+
+static int launch_layer(qxd_ctx* ctx, int fl, const float4* a, int cin, const float2* W, float4* out, int cout,
+                        cudaStream_t st) {
+    const Geo& g = ctx->g;
+    dim3 grid(nblocks(g.Vh, kPtcThreads), 2, cout);
+    const size_t smem = (size_t)cin * 9 * 16 * sizeof(float2);
+    ProfScope prof(ctx, "ptc_layer", (double)chan_bytes(ctx) * (cin * 9 + cout) + 2.0 * g.Vh * 4 * 56, st);
+    k_ptc_layer<<<grid, kPtcThreads, smem, st>>>(g, links_of(ctx, fl), a, cin, W, out);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+// Forward pass: acts[0] = embedded input (1 channel); acts[l+1] = layer l (acts[l])
+static int ptc_forward(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, float4* const* acts,
+                       cudaStream_t st) {
+    const float2* w = W;
+    for (int l = 0; l < nlayers; ++l) {
+        int ci, co;
+        layer_shape(l, nlayers, nch, &ci, &co);
+        QXD_TRY(launch_layer(ctx, fl, acts[l], ci, w, acts[l + 1], co, st));
+        w += layer_weights(ci, co);
+    }
+    return QXD_OK;
+}
+
+static int check_shape(qxd_ctx* ctx, int nlayers, int nch) {
+    if (nlayers < 1 || nlayers > 8 || nch < 1 || nch > kPtcMaxCh)
+        return qxd_fail(ctx, QXD_EARG, "learned preconditioner: 1..8 layers of 1..16 channels");
+    return QXD_OK;
+}
+
+// Activation buffers of one pass: acts[0..nlayers] (channel counts 1, nch.., 1)
+static int ptc_buffers(qxd_ctx* ctx, int nlayers, int nch, int slot0, std::vector<float4*>& acts) {
+    acts.resize(nlayers + 1);
+    for (int l = 0; l <= nlayers; ++l) {
+        const int ch = (l == 0 || l == nlayers) ? 1 : nch;
+        void* p;
+        QXD_TRY(qxd_ws(ctx, slot0 + l, chan_bytes(ctx) * ch, &p));
+        acts[l] = static_cast<float4*>(p);
+    }
+    return QXD_OK;
+}
+
+// z_e = (M r_e)_e for FP32 internal even fields
+int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const void* r_e, void* z_e,
+                       cudaStream_t st) {
+    std::vector<float4*> acts;
+    QXD_TRY(ptc_buffers(ctx, nlayers, nch, WS_PTC, acts));
+    const size_t hb = half_bytes(ctx, QXD_FP32);
+    QXD_CUDA(ctx, cudaMemcpyAsync(acts[0], r_e, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(acts[0]) + hb, 0, hb, st));
+    QXD_TRY(ptc_forward(ctx, fl, W, nlayers, nch, acts.data(), st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(z_e, acts[nlayers], hb, cudaMemcpyDeviceToDevice, st));
+    return QXD_OK;
+}
+
+// Loss and gradient over pairs (internal FP32 even fields r[i], e[i]); G accumulated
+// (complex, layout of W).  Returns the summed loss in *loss.
+static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const char* r,
+                                  const char* e, const double* ee, const int* idx, int nb, float2* G, double* loss,
+                                  cudaStream_t st) {
+    const Geo& g = ctx->g;
+    const size_t hb = half_bytes(ctx, QXD_FP32);
+    const size_t n = 12ull * g.Vh;
+    std::vector<float4*> acts;
+    QXD_TRY(ptc_buffers(ctx, nlayers, nch, WS_PTC, acts));
+    void *dA, *dB, *Wa, *part;
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 10, chan_bytes(ctx) * nch, &dA));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 11, chan_bytes(ctx) * nch, &dB));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 12, layer_weights(nch, nch) * sizeof(float2), &Wa));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 13, (size_t)nch * nch * 9 * kWgBlocks * 32 * sizeof(double), &part));
+    // offsets of each layer's weights
+    std::vector<size_t> off(nlayers + 1, 0);
+    for (int l = 0; l < nlayers; ++l) {
+        int ci, co;
+        layer_shape(l, nlayers, nch, &ci, &co);
+        off[l + 1] = off[l] + layer_weights(ci, co);
+    }
+    double tot = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        const int i = idx[k];
+        QXD_CUDA(ctx, cudaMemcpyAsync(acts[0], r + (size_t)i * hb, hb, cudaMemcpyDeviceToDevice, st));
+        QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(acts[0]) + hb, 0, hb, st));
+        QXD_TRY(ptc_forward(ctx, fl, W, nlayers, nch, acts.data(), st));
+        // delta = ((M r)_e - e) / |e|^2 on even sites, 0 on odd sites
+        float4* delta = static_cast<float4*>(dA);
+        QXD_CUDA(ctx, cudaMemcpyAsync(delta, acts[nlayers], hb, cudaMemcpyDeviceToDevice, st));
+        QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(delta) + hb, 0, hb, st));
+        QXD_TRY(blas_axpby(ctx, 1, 1, n, -1.0, 0.0, e + (size_t)i * hb, 1.0, 0.0, delta, st));
+        QXD_TRY(blas_norm2(ctx, 1, n, delta, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        if (ctx->red_host[1] != 0.0) return qxd_fail(ctx, QXD_ENAN, "learned preconditioner: non-finite output");
+        tot += ctx->red_host[0] / ee[i];
+        QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, delta, 1.0 / ee[i], 0.0, delta, st));
+        if (!G) continue;
+        float4* dcur = delta;
+        float4* dnext = static_cast<float4*>(dB);
+        for (int l = nlayers - 1; l >= 0; --l) {
+            int ci, co;
+            layer_shape(l, nlayers, nch, &ci, &co);
+            const int nq = co * ci * 9;
+            {
+                ProfScope prof(ctx, "ptc_wgrad", (double)chan_bytes(ctx) * (ci + co) * 9, st);
+                dim3 grid(kWgBlocks, nq);
+                k_ptc_wgrad<<<grid, kPtcThreads, 0, st>>>(g, links_of(ctx, fl), dcur, acts[l], ci,
+                                                          static_cast<double*>(part));
+                QXD_CUDA(ctx, cudaGetLastError());
+                k_ptc_wgrad_final<<<nblocks(nq * 16, 256), 256, 0, st>>>(static_cast<double*>(part), nq, kWgBlocks,
+                                                                       G + off[l], 1);
+                QXD_CUDA(ctx, cudaGetLastError());
+            }
+            if (l > 0) {
+                k_ptc_adjoint_weights<<<nblocks(nq, 128), 128, 0, st>>>(W + off[l], ci, co,
+                                                                        static_cast<float2*>(Wa));
+                QXD_CUDA(ctx, cudaGetLastError());
+                QXD_TRY(launch_layer(ctx, fl, dcur, co, static_cast<float2*>(Wa), dnext, ci, st));
+                std::swap(dcur, dnext);
+            }
+        }
+    }
+    *loss = tot;
+    return QXD_OK;
+}
+
+// pack canonical complex64 even fields into internal FP32 fields and their norms
+static int pack_pairs(qxd_ctx* ctx, const void* r, const void* e, int npairs, char** R, char** E,
+                      std::vector<double>& ee, cudaStream_t st) {
+    const size_t hb = half_bytes(ctx, QXD_FP32);
+    const size_t cb = (size_t)ctx->g.Vh * 12 * 8;
+    void *dr, *de, *pr, *pe;
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 20, cb * npairs, &dr));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 21, cb * npairs, &de));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 22, hb * npairs, &pr));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 23, hb * npairs, &pe));
+    QXD_CUDA(ctx, cudaMemcpyAsync(dr, r, cb * npairs, cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(de, e, cb * npairs, cudaMemcpyDefault, st));
+    QXD_TRY(launch_pack(ctx, 1, dr, 0, 0, QXD_FP32, pr, npairs, st));
+    QXD_TRY(launch_pack(ctx, 1, de, 0, 0, QXD_FP32, pe, npairs, st));
+    *R = static_cast<char*>(pr);
+    *E = static_cast<char*>(pe);
+    ee.resize(npairs);
+    const size_t n = 12ull * ctx->g.Vh;
+    for (int i = 0; i < npairs; ++i) {
+        QXD_TRY(blas_norm2(ctx, 1, n, *E + (size_t)i * hb, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        if (!(ctx->red_host[0] > 0.0) || ctx->red_host[1] != 0.0)
+            return qxd_fail(ctx, QXD_EARG, "learned preconditioner: error vectors must be finite and non-zero");
+        ee[i] = ctx->red_host[0];
+    }
+    return QXD_OK;
+}
+
+static int weights_on_device(qxd_ctx* ctx, const float* W, size_t nw, int slot, float2** out, cudaStream_t st) {
+    void* d;
+    QXD_TRY(qxd_ws(ctx, slot, nw * sizeof(float2), &d));
+    QXD_CUDA(ctx, cudaMemcpyAsync(d, W, nw * sizeof(float2), cudaMemcpyDefault, st));
+    *out = static_cast<float2*>(d);
+    return QXD_OK;
+}
+
+}  // namespace qxd
+
+using namespace qxd;
+
+static int ptc_check(qxd_ctx* ctx, int fl) {
+    if (!ctx) return QXD_EARG;
+    if (fl < 0 || fl >= QXD_MAX_FLAVOURS) return qxd_fail(ctx, QXD_EARG, "flavour id out of range 0..7");
+    if (!ctx->links_set || !ctx->fl[fl].set)
+        return qxd_fail(ctx, QXD_ESTATE, "learned preconditioner: links and SW term must be set first");
+    cudaSetDevice(ctx->device);
+    return QXD_OK;
+}
+
+extern "C" {
+
+int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch) {
+    QXD_TRY(ptc_check(ctx, fl));
+    QXD_TRY(check_shape(ctx, nlayers, nch));
+    if (!W) return qxd_fail(ctx, QXD_EARG, "set_precond_weights: NULL weights");
+    QxdFlavour& F = ctx->fl[fl];
+    const size_t nw = ptc_weight_count(nlayers, nch);
+    cudaFree(F.W);
+    F.W = nullptr;
+    if (cudaMalloc(&F.W, nw * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return qxd_fail(ctx, QXD_ENOMEM, "set_precond_weights: allocation failed");
+    }
+    QXD_CUDA(ctx, cudaMemcpy(F.W, W, nw * sizeof(float2), cudaMemcpyDefault));
+    F.nlayers = nlayers;
+    F.nch = nch;
+    return QXD_OK;
+}
+
+int qxd_ptc_apply(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* in_e, void* out_e,
+                  void* stream) {
+    QXD_TRY(ptc_check(ctx, fl));
+    QXD_TRY(check_shape(ctx, nlayers, nch));
+    if (!W || !in_e || !out_e) return qxd_fail(ctx, QXD_EARG, "ptc_apply: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t cb = (size_t)ctx->g.Vh * 12 * 8;
+    const size_t hb = half_bytes(ctx, QXD_FP32);
+    float2* Wd;
+    QXD_TRY(weights_on_device(ctx, W, ptc_weight_count(nlayers, nch), WS_PTC + 30, &Wd, st));
+    void *ci, *ri, *zi, *co;
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 31, cb, &ci));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 32, hb, &ri));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 33, hb, &zi));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 34, cb, &co));
+    QXD_CUDA(ctx, cudaMemcpyAsync(ci, in_e, cb, cudaMemcpyDefault, st));
+    QXD_TRY(launch_pack(ctx, 1, ci, 0, 0, QXD_FP32, ri, 1, st));
+    QXD_TRY(ptc_apply_internal(ctx, fl, Wd, nlayers, nch, ri, zi, st));
+    QXD_TRY(launch_unpack(ctx, QXD_FP32, zi, 0, 1, co, 0, 1, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(out_e, co, cb, cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    return QXD_OK;
+}
+
+int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* r, const void* e,
+                      int npairs, double* loss, float* grad, void* stream) {
+    QXD_TRY(ptc_check(ctx, fl));
+    QXD_TRY(check_shape(ctx, nlayers, nch));
+    if (!W || !r || !e || npairs < 1 || !loss) return qxd_fail(ctx, QXD_EARG, "ptc_loss_grad: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nw = ptc_weight_count(nlayers, nch);
+    float2* Wd;
+    QXD_TRY(weights_on_device(ctx, W, nw, WS_PTC + 30, &Wd, st));
+    char *R, *E;
+    std::vector<double> ee;
+    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, st));
+    void* G = nullptr;
+    if (grad) {
+        QXD_TRY(qxd_ws(ctx, WS_PTC + 35, nw * sizeof(float2), &G));
+        QXD_CUDA(ctx, cudaMemsetAsync(G, 0, nw * sizeof(float2), st));
+    }
+    std::vector<int> idx(npairs);
+    for (int i = 0; i < npairs; ++i) idx[i] = i;
+    QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), idx.data(), npairs,
+                                   static_cast<float2*>(G), loss, st));
+    if (grad) QXD_CUDA(ctx, cudaMemcpyAsync(grad, G, nw * sizeof(float2), cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    return QXD_OK;
+}
+
+int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayers, int nch, const void* r,
+                  const void* e, int npairs, int batch, int nsteps, double lr, int* t, double* losses, void* stream) {
+    QXD_TRY(ptc_check(ctx, fl));
+    QXD_TRY(check_shape(ctx, nlayers, nch));
+    if (!W || !m || !v || !r || !e || !t || npairs < 1 || batch < 1 || nsteps < 0 || !(lr > 0.0))
+        return qxd_fail(ctx, QXD_EARG, "ptc_train: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nw = ptc_weight_count(nlayers, nch);
+    float2 *Wd, *md, *vd;
+    QXD_TRY(weights_on_device(ctx, W, nw, WS_PTC + 30, &Wd, st));
+    QXD_TRY(weights_on_device(ctx, m, nw, WS_PTC + 36, &md, st));
+    QXD_TRY(weights_on_device(ctx, v, nw, WS_PTC + 37, &vd, st));
+    char *R, *E;
+    std::vector<double> ee;
+    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, st));
+    void* G;
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 35, nw * sizeof(float2), &G));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    std::vector<int> idx(batch);
+    for (int s = 0; s < nsteps; ++s) {
+        for (int k = 0; k < batch; ++k) idx[k] = (s * batch + k) % npairs;
+        QXD_CUDA(ctx, cudaMemsetAsync(G, 0, nw * sizeof(float2), st));
+        double L = 0.0;
+        QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), idx.data(), batch,
+                                       static_cast<float2*>(G), &L, st));
+        if (losses) losses[s] = L / batch;
+        *t += 1;
+        const float c1 = 1.f - std::pow(b1, (float)*t), c2 = 1.f - std::pow(b2, (float)*t);
+        ProfScope prof(ctx, "ptc_adam", 4.0 * 2 * nw * 4, st);
+        k_adam<<<nblocks(2 * nw, 256), 256, 0, st>>>(reinterpret_cast<float*>(Wd), static_cast<const float*>(G),
+                                                     reinterpret_cast<float*>(md), reinterpret_cast<float*>(vd),
+                                                     2 * nw, 1.f / batch, (float)lr, b1, b2, eps, c1, c2);
+        QXD_CUDA(ctx, cudaGetLastError());
+    }
+    QXD_CUDA(ctx, cudaMemcpyAsync(W, Wd, nw * sizeof(float2), cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(m, md, nw * sizeof(float2), cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(v, vd, nw * sizeof(float2), cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    return QXD_OK;
+}
+
+int qxd_ptc_record_pairs(qxd_ctx* ctx, int fl, const void* b, int npairs, int stride, void* r_out, void* e_out,
+                         void* stream) {
+    QXD_TRY(ptc_check(ctx, fl));
+    if (!b || !r_out || !e_out || npairs < 1 || stride < 1) return qxd_fail(ctx, QXD_EARG, "ptc_record_pairs: bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, QXD_FP64);
+    const size_t cb64 = (size_t)ctx->g.Vh * 12 * 16, cb32 = (size_t)ctx->g.Vh * 12 * 8;
+    void *cbuf, *bb, *y, *s, *z, *p, *w, *to, *ys, *c32;
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 40, cb64, &cbuf));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 41, hb, &bb));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 42, hb, &y));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 43, hb, &s));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 44, hb, &z));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 45, hb, &p));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 46, hb, &w));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 47, hb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 48, hb * npairs, &ys));      // iterates x_k (FP64)
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 49, 2 * cb32 * npairs, &c32));  // canonical r, e (complex64)
+    QXD_CUDA(ctx, cudaMemcpyAsync(cbuf, b, cb64, cudaMemcpyDefault, st));
+    QXD_TRY(launch_pack(ctx, 0, cbuf, 0, 0, QXD_FP64, bb, 1, st));
+    // CGNR on Dhat y = b (y = 0), recording (s_k, y_k) every `stride` iterations
+    QXD_CUDA(ctx, cudaMemsetAsync(y, 0, hb, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(s, bb, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(op_Dhat(ctx, fl, 0, 1, s, z, to, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(p, z, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, bb, 0, st));
+    QXD_TRY(blas_norm2(ctx, 0, n, z, 2, st));
+    QXD_TRY(blas_fetch(ctx, 4, st));
+    const double bn = std::sqrt(ctx->red_host[0]);
+    double zz = ctx->red_host[2];
+    if (!(bn > 0.0) || ctx->red_host[1] != 0.0) return qxd_fail(ctx, QXD_EARG, "ptc_record_pairs: bad source");
+    char* R32 = static_cast<char*>(c32);
+    char* E32 = R32 + cb32 * npairs;
+    int rec = 0;
+    const int nmx = 100000;
+    bool conv = false;
+    for (int k = 1; k <= nmx; ++k) {
+        QXD_TRY(op_Dhat(ctx, fl, 0, 0, p, w, to, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, w, 0, st));
+        QXD_TRY(blas_fetch(ctx, 2, st));
+        const double alpha = zz / ctx->red_host[0];
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, alpha, 0.0, p, 1.0, 0.0, y, st));
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, -alpha, 0.0, w, 1.0, 0.0, s, st));
+        if (rec < npairs && k % stride == 0) {
+            // r_k = s_k (the residual b - Dhat y_k), keep y_k for e_k = x* - y_k
+            QXD_TRY(launch_unpack(ctx, QXD_FP64, s, 0, 1, R32 + (size_t)rec * cb32, 0, 1, st));
+            QXD_CUDA(ctx, cudaMemcpyAsync(static_cast<char*>(ys) + (size_t)rec * hb, y, hb, cudaMemcpyDeviceToDevice,
+                                          st));
+            ++rec;
+        }
+        QXD_TRY(op_Dhat(ctx, fl, 0, 1, s, z, to, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, s, 0, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, z, 2, st));
+        QXD_TRY(blas_fetch(ctx, 4, st));
+        if (std::sqrt(ctx->red_host[0]) <= 1e-10 * bn) {
+            conv = true;
+            break;
+        }
+        const double beta = ctx->red_host[2] / zz;
+        zz = ctx->red_host[2];
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, z, beta, 0.0, p, st));
+    }
+    if (!conv) return qxd_fail(ctx, QXD_ENOCONV, "ptc_record_pairs: CGNR did not converge");
+    if (rec < npairs) return qxd_fail(ctx, QXD_EARG, "ptc_record_pairs: fewer iterations than npairs * stride");
+    // e_i = x* - y_i
+    for (int i = 0; i < npairs; ++i) {
+        char* yi = static_cast<char*>(ys) + (size_t)i * hb;
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, y, -1.0, 0.0, yi, st));
+        QXD_TRY(launch_unpack(ctx, QXD_FP64, yi, 0, 1, E32 + (size_t)i * cb32, 0, 1, st));
+    }
+    QXD_CUDA(ctx, cudaMemcpyAsync(r_out, R32, cb32 * npairs, cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(e_out, E32, cb32 * npairs, cudaMemcpyDefault, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    return QXD_OK;
+}
+
+}  // extern "C"

@@ -21,7 +21,7 @@ struct QxdFlavour {
     double2* C64[2] = {nullptr, nullptr};  // [p][36][Vh]  diag term, inverse
     float4* C32[2] = {nullptr, nullptr};   // [p][18][Vh]
     // learned preconditioner
-    float* W = nullptr;        // device weights
+    void* W = nullptr;         // device weights (complex float [layers][cout][cin][9][4][4])
     int nlayers = 0, nch = 0;
 };
 

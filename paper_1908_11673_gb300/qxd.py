@@ -25,6 +25,7 @@ STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: 
 
 EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_apply_Dw",
            "qxd_apply_Dhat_eo", "qxd_apply_Dhat_eo_noalloc", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
+           "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -79,6 +80,10 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_solve": (i, [vp, i, ctypes.POINTER(Solver), vp, vp, i, ctypes.POINTER(Info), vp]),
         "qxd_solve_multishift": (i, [vp, i, i, vp, ctypes.POINTER(Solver), vp, vp, ctypes.POINTER(Info), vp]),
         "qxd_set_precond_weights": (i, [vp, i, vp, i, i]),
+        "qxd_ptc_apply": (i, [vp, i, vp, i, i, vp, vp, vp]),
+        "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(d), vp, vp]),
+        "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, ctypes.POINTER(i), vp, vp]),
+        "qxd_ptc_record_pairs": (i, [vp, i, vp, i, i, vp, vp, vp]),
         "qxd_profile": (i, [vp, i]),
         "qxd_profile_entry": (i, [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -197,6 +202,32 @@ class Context:
         if check:
             self._check(rc)
         return info
+
+    # ---- learned preconditioner ------------------------------------------------
+    def ptc_apply(self, fl, W, nlayers, nch, inp, out, stream=None):
+        self._check(self.lib.qxd_ptc_apply(self._h, int(fl), _ptr(W), int(nlayers), int(nch), _ptr(inp), _ptr(out),
+                                           _stream(stream)))
+
+    def ptc_loss_grad(self, fl, W, nlayers, nch, r, e, npairs, grad=None, stream=None):
+        loss = ctypes.c_double()
+        self._check(self.lib.qxd_ptc_loss_grad(self._h, int(fl), _ptr(W), int(nlayers), int(nch), _ptr(r), _ptr(e),
+                                               int(npairs), ctypes.byref(loss), _ptr(grad), _stream(stream)))
+        return loss.value
+
+    def ptc_train(self, fl, W, m, v, nlayers, nch, r, e, npairs, batch, nsteps, lr, t, stream=None):
+        """Adam steps on (W, m, v) in place; t is a one-element int32 array (step counter).
+        Returns the per-step mean losses."""
+        losses = np.zeros(max(nsteps, 1), dtype=np.float64)
+        tc = ctypes.c_int(int(t[0]))
+        self._check(self.lib.qxd_ptc_train(self._h, int(fl), _ptr(W), _ptr(m), _ptr(v), int(nlayers), int(nch),
+                                           _ptr(r), _ptr(e), int(npairs), int(batch), int(nsteps), float(lr),
+                                           ctypes.byref(tc), losses.ctypes.data, _stream(stream)))
+        t[0] = tc.value
+        return losses[:nsteps]
+
+    def ptc_record_pairs(self, fl, b, npairs, stride, r_out, e_out, stream=None):
+        self._check(self.lib.qxd_ptc_record_pairs(self._h, int(fl), _ptr(b), int(npairs), int(stride), _ptr(r_out),
+                                                  _ptr(e_out), _stream(stream)))
 
     def profile(self, mode):
         """0 off, 1 count kernel launches, 2 count and time them (resets the counters)."""
