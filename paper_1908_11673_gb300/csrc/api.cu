@@ -38,7 +38,7 @@ int qxd_ws(qxd_ctx* ctx, int slot, size_t bytes, void** out) {
 }
 
 // ---- profiling -------------------------------------------------------------------
-ProfScope::ProfScope(qxd_ctx* c, const char* name, double bytes, cudaStream_t s) : ctx(c), st(s) {
+ProfScope::ProfScope(qxd_ctx* c, const char* name, double bytes, cudaStream_t s, int nlaunch) : ctx(c), st(s) {
     if (!ctx || ctx->prof_mode == 0) return;
     auto it = ctx->prof_idx.find(name);
     if (it == ctx->prof_idx.end()) {
@@ -49,7 +49,7 @@ ProfScope::ProfScope(qxd_ctx* c, const char* name, double bytes, cudaStream_t s)
     } else {
         cls = it->second;
     }
-    ctx->prof_cls[cls].launches += 1;
+    ctx->prof_cls[cls].launches += nlaunch;
     ctx->prof_cls[cls].bytes += bytes;
     if (ctx->prof_mode >= 2) {
         for (cudaEvent_t* e : {&a, &b}) {
@@ -203,6 +203,7 @@ void qxd_destroy(qxd_ctx* ctx) {
     for (void* p : ctx->ws_ptr) cudaFree(p);
     prof_resolve(ctx);
     for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     cudaFree(ctx->red_partials);
     cudaFree(ctx->red_result);
     cudaFree(ctx->dev_flag);

@@ -565,6 +565,127 @@ int blas_msg_update(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr,
     return QXD_OK;
 }
 
+// ---- device-scalar variants ----------------------------------------------------------
+template <int P>
+__global__ void k_axpby_dev(size_t nch, const double* __restrict__ c, const void* __restrict__ x,
+                            void* __restrict__ y) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    const R a = (R)c[0], b = (R)c[1];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> xv[NC], yv[NC];
+        Chunk<P>::ld(x, i, xv);
+        Chunk<P>::ld(y, i, yv);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            yv[q].re = fma(a, xv[q].re, b * yv[q].re);
+            yv[q].im = fma(a, xv[q].im, b * yv[q].im);
+        }
+        Chunk<P>::st(y, i, yv);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kRedThreads) k_axpy_norm_dev(size_t nch, const double* __restrict__ c,
+                                                               const void* __restrict__ x, void* __restrict__ y,
+                                                               RedOut o) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    const R a = (R)c[0];
+    double v[2] = {0.0, 0.0};
+    R f = R(0);
+    int cnt = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> xv[NC], yv[NC];
+        Chunk<P>::ld(x, i, xv);
+        Chunk<P>::ld(y, i, yv);
+        R s = R(0);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            yv[q].re = fma(a, xv[q].re, yv[q].re);
+            yv[q].im = fma(a, xv[q].im, yv[q].im);
+            s = fma(yv[q].re, yv[q].re, fma(yv[q].im, yv[q].im, s));
+        }
+        Chunk<P>::st(y, i, yv);
+        if (isfinite(s)) f += s;
+        else v[1] += 1.0;
+        if (++cnt == kFlush) {
+            v[0] += f;
+            f = R(0);
+            cnt = 0;
+        }
+    }
+    v[0] += f;
+    block_reduce_finish<2>(v, o);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_msg_update_dev(size_t nch, int ns, ShiftPtrs ptr, ShiftCoefDev c,
+                                                        const void* __restrict__ r) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> rv[NC];
+        Chunk<P>::ld(r, i, rv);
+        for (int j = 0; j < ns; ++j) {
+            if (!c.upd[j]) continue;
+            cplx<R> xv[NC], pv[NC];
+            Chunk<P>::ld(ptr.x[j], i, xv);
+            Chunk<P>::ld(ptr.p[j], i, pv);
+            const R a = (R)c.alpha[j], z = (R)c.zeta[j], bb = (R)c.beta[j];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+                xv[q].re = fma(a, pv[q].re, xv[q].re);
+                xv[q].im = fma(a, pv[q].im, xv[q].im);
+                pv[q].re = fma(z, rv[q].re, bb * pv[q].re);
+                pv[q].im = fma(z, rv[q].im, bb * pv[q].im);
+            }
+            Chunk<P>::st(ptr.x[j], i, xv);
+            Chunk<P>::st(ptr.p[j], i, pv);
+        }
+    }
+}
+
+int blas_axpby_dev(qxd_ctx* ctx, int P, size_t n, const double* c, const void* x, void* y, cudaStream_t st) {
+    const size_t nc = nchunks(P, n);
+    const int nb = upd_blocks(ctx, nc);
+    ProfScope prof(ctx, "axpby", (double)n * 3 * eb(P), st);
+    if (P == 0) k_axpby_dev<0><<<nb, 256, 0, st>>>(nc, c, x, y);
+    else if (P == 1) k_axpby_dev<1><<<nb, 256, 0, st>>>(nc, c, x, y);
+    else k_axpby_dev<2><<<nb, 256, 0, st>>>(nc, c, x, y);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+int blas_axpy_norm_dev(qxd_ctx* ctx, int P, size_t n, const double* c, const void* x, void* y, int slot,
+                       cudaStream_t st) {
+    const size_t nc = nchunks(P, n);
+    ProfScope prof(ctx, "multi_axpy_norm", (double)n * 3 * eb(P), st);
+    const RedOut o = red_out(ctx, slot);
+    const size_t wpb = (size_t)kRedThreads * 2;
+#define QXD_LAUNCH(Q) \
+    k_axpy_norm_dev<Q><<<wave_blocks(ctx, k_axpy_norm_dev<Q>, kRedThreads, wpb, nc), kRedThreads, 0, st>>>(nc, c, x, y, o)
+    if (P == 0) QXD_LAUNCH(0);
+    else if (P == 1) QXD_LAUNCH(1);
+    else QXD_LAUNCH(2);
+#undef QXD_LAUNCH
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+int blas_msg_update_dev(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr, const ShiftCoefDev& c,
+                        const void* r, cudaStream_t st) {
+    if (ns < 1 || ns > kMaxShifts) return qxd_fail(ctx, QXD_EARG, "msg_update: shift count out of range");
+    const size_t nc = nchunks(P, n);
+    const int nb = upd_blocks(ctx, nc);
+    ProfScope prof(ctx, "msg_update", (double)n * eb(P) * (1 + 4 * ns), st);
+    if (P == 0) k_msg_update_dev<0><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    else if (P == 1) k_msg_update_dev<1><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    else k_msg_update_dev<2><<<nb, 256, 0, st>>>(nc, ns, ptr, c, r);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
 int blas_fetch(qxd_ctx* ctx, int nslots, cudaStream_t st) {
     QXD_CUDA(ctx, cudaMemcpyAsync(ctx->red_host, ctx->red_result, sizeof(double) * nslots, cudaMemcpyDeviceToHost, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));

@@ -43,6 +43,14 @@ int blas_multi_axpy_norm(qxd_ctx* ctx, int p, size_t n, int k, const double* cre
                          const void* const* X, void* y, int slot, cudaStream_t st);
 int blas_fetch(qxd_ctx* ctx, int nslots, cudaStream_t st);
 
+// Variants whose scalars live in device memory (no host round trip; usable
+// inside captured CUDA graphs):
+// y = c[0] x + c[1] y  (real coefficients read from the device array c)
+int blas_axpby_dev(qxd_ctx* ctx, int P, size_t n, const double* c, const void* x, void* y, cudaStream_t st);
+// y += c[0] x, then result[slot] = |y|^2
+int blas_axpy_norm_dev(qxd_ctx* ctx, int P, size_t n, const double* c, const void* x, void* y, int slot,
+                       cudaStream_t st);
+
 }  // namespace qxd
 
 namespace qxd {
@@ -62,5 +70,16 @@ struct ShiftCoef {
 };
 int blas_msg_update(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr, const ShiftCoef& c, const void* r,
                     cudaStream_t st);
+
+// Same update with coefficients in device memory: for j < ns with upd[j] != 0,
+// x_j += alpha[j] p_j; p_j = zeta[j] r + beta[j] p_j
+struct ShiftCoefDev {
+    const double* alpha;
+    const double* zeta;
+    const double* beta;
+    const int* upd;
+};
+int blas_msg_update_dev(qxd_ctx* ctx, int P, size_t n, int ns, const ShiftPtrs& ptr, const ShiftCoefDev& c,
+                        const void* r, cudaStream_t st);
 
 }  // namespace qxd

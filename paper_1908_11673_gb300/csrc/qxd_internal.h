@@ -63,6 +63,7 @@ struct qxd_ctx {
     // autotuned (rhs per thread, threads per block) of the multi-RHS hopping kernel,
     // keyed by (precision, self mode, post mode, nrhs, V/2)
     std::map<std::tuple<int, int, int, int, long long>, std::pair<int, int>> tune_hop;
+    cudaStream_t cap_stream = nullptr;  // library stream for CUDA-graph capture
 };
 
 // Brackets one kernel launch when profiling is on: counts it under `name` with
@@ -74,7 +75,7 @@ struct ProfScope {
     cudaEvent_t b = nullptr;
     cudaEvent_t a = nullptr;
     cudaStream_t st;
-    ProfScope(qxd_ctx* c, const char* name, double bytes, cudaStream_t s);
+    ProfScope(qxd_ctx* c, const char* name, double bytes, cudaStream_t s, int nlaunch = 1);
     ~ProfScope();
 };
 

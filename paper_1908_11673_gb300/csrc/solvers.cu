@@ -513,6 +513,193 @@ static int mscg_core(qxd_ctx* ctx, int fl, int P, int ns, const double* sigma, c
     return QXD_OK;
 }
 
+// ---- multi-shift CG with device-resident scalars, captured as a CUDA graph ---------
+// The scalars of the recursion (alpha, beta, zeta_j, ...) live in device memory and
+// are updated by two one-thread kernels, so an iteration is a fixed sequence of
+// launches with no host round trip.  kGraphIters iterations are captured once
+// into a graph, which is then replayed; the host reads the number of active
+// shifts after each replay.  Iterations after convergence are no-ops (alpha = 0).
+constexpr int kGraphIters = 8;
+
+struct MscgDev {
+    double rr, alpha, alpha_prev, beta_prev, bn, tol;
+    double coef_r[2];  // {-alpha, 0}: r += coef_r[0] A p
+    double coef_p[2];  // {1, beta}:   p = r + beta p
+    double ds[kMaxShifts], zp[kMaxShifts], z[kMaxShifts], zn[kMaxShifts];
+    double aj[kMaxShifts], zj[kMaxShifts], bj[kMaxShifts];
+    int active[kMaxShifts], upd[kMaxShifts];
+    int nactive, iter;
+};
+
+__global__ void k_mscg_alpha(MscgDev* s, const double* __restrict__ red, int ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double pAp = red[0];
+    const double alpha = (s->nactive > 0 && pAp > 0.0 && s->rr > 0.0) ? s->rr / pAp : 0.0;
+    s->alpha = alpha;
+    s->coef_r[0] = -alpha;
+    s->coef_r[1] = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        if (!s->active[j] || alpha == 0.0) {
+            s->aj[j] = 0.0;
+            continue;
+        }
+        const double den = alpha * s->beta_prev * (s->zp[j] - s->z[j]) +
+                           s->zp[j] * s->alpha_prev * (1.0 + s->ds[j] * alpha);
+        s->zn[j] = den != 0.0 ? s->z[j] * s->zp[j] * s->alpha_prev / den : 0.0;
+        s->aj[j] = s->z[j] != 0.0 ? alpha * s->zn[j] / s->z[j] : 0.0;
+    }
+}
+
+__global__ void k_mscg_beta(MscgDev* s, const double* __restrict__ red, int ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double rr_new = red[2];
+    const bool step = s->alpha != 0.0;
+    const double beta = (step && s->rr > 0.0) ? rr_new / s->rr : 0.0;
+    int na = 0;
+    for (int j = 0; j < ns; ++j) {
+        s->upd[j] = step && s->active[j];
+        if (!s->upd[j]) continue;
+        const double q = s->z[j] != 0.0 ? s->zn[j] / s->z[j] : 0.0;
+        s->bj[j] = beta * q * q;
+        s->zj[j] = s->zn[j];
+        if (fabs(s->zn[j]) * sqrt(rr_new) <= s->tol * s->bn) s->active[j] = 0;
+        s->zp[j] = s->z[j];
+        s->z[j] = s->zn[j];
+    }
+    for (int j = 0; j < ns; ++j) na += s->active[j];
+    s->nactive = na;
+    if (step) {
+        s->rr = rr_new;
+        s->alpha_prev = s->alpha;
+        s->beta_prev = beta;
+        s->iter += 1;
+    }
+    s->coef_p[0] = 1.0;
+    s->coef_p[1] = beta;
+}
+
+static int mscg_iteration_dev(qxd_ctx* ctx, int fl, int P, int ns, double s0, MscgDev* dstate, const ShiftPtrs& sp,
+                              void* r, void* pb, void* Ap, void* te, void* to, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    QXD_TRY(op_normal(ctx, fl, P, s0, pb, Ap, te, to, st));
+    QXD_TRY(blas_dot(ctx, P, P, n, pb, Ap, 0, st));
+    k_mscg_alpha<<<1, 32, 0, st>>>(dstate, ctx->red_result, ns);
+    QXD_CUDA(ctx, cudaGetLastError());
+    QXD_TRY(blas_axpy_norm_dev(ctx, P, n, dstate->coef_r, Ap, r, 2, st));
+    k_mscg_beta<<<1, 32, 0, st>>>(dstate, ctx->red_result, ns);
+    QXD_CUDA(ctx, cudaGetLastError());
+    ShiftCoefDev c{dstate->aj, dstate->zj, dstate->bj, dstate->upd};
+    QXD_TRY(blas_msg_update_dev(ctx, P, n, ns, sp, c, r, st));
+    QXD_TRY(blas_axpby_dev(ctx, P, n, dstate->coef_p, r, pb, st));
+    return QXD_OK;
+}
+
+static bool graphs_enabled() {
+    const char* e = std::getenv("QXD_GRAPHS");
+    return !(e && e[0] == '0');
+}
+
+static int mscg_core_graph(qxd_ctx* ctx, int fl, int P, int ns, const double* sigma, const void* b, char* X,
+                           int max_iter, double tol, int* iters, cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *r, *pb, *Ap, *te, *to, *Pblk, *dsv;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 110, hb, &r));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 111, hb, &pb));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 112, hb, &Ap));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 113, hb, &te));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 114, hb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 109, hb * ns, &Pblk));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 122, sizeof(MscgDev), &dsv));
+    MscgDev* dstate = static_cast<MscgDev*>(dsv);
+    char* Pc = static_cast<char*>(Pblk);
+    QXD_CUDA(ctx, cudaMemsetAsync(X, 0, hb * ns, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(pb, b, hb, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < ns; ++j) QXD_CUDA(ctx, cudaMemcpyAsync(Pc + j * hb, b, hb, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_TRY(blas_fetch(ctx, 2, st));
+    QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "MSCG source"));
+    *iters = 0;
+    if (!(ctx->red_host[0] > 0.0)) return QXD_OK;
+    double s0 = sigma[0];
+    for (int j = 1; j < ns; ++j) s0 = std::min(s0, sigma[j]);
+    MscgDev h{};
+    h.rr = ctx->red_host[0];
+    h.bn = std::sqrt(h.rr);
+    h.tol = tol;
+    h.alpha_prev = 1.0;
+    h.beta_prev = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        h.ds[j] = sigma[j] - s0;
+        h.zp[j] = h.z[j] = 1.0;
+        h.active[j] = 1;
+    }
+    h.nactive = ns;
+    QXD_CUDA(ctx, cudaMemcpyAsync(dstate, &h, sizeof h, cudaMemcpyHostToDevice, st));
+    ShiftPtrs sp;
+    for (int j = 0; j < ns; ++j) {
+        sp.x[j] = X + j * hb;
+        sp.p[j] = Pc + j * hb;
+    }
+    // first iteration eagerly (it also settles the autotuned kernel shapes)
+    QXD_TRY(mscg_iteration_dev(ctx, fl, P, ns, s0, dstate, sp, r, pb, Ap, te, to, st));
+    if (!ctx->cap_stream) QXD_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    const int prof_mode = ctx->prof_mode;
+    ctx->prof_mode = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = QXD_OK;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        ctx->prof_mode = prof_mode;
+        return qxd_fail(ctx, QXD_ECUDA, "MSCG: cannot start graph capture");
+    }
+    for (int k = 0; k < kGraphIters && rc == QXD_OK; ++k)
+        rc = mscg_iteration_dev(ctx, fl, P, ns, s0, dstate, sp, r, pb, Ap, te, to, ctx->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    ctx->prof_mode = prof_mode;
+    if (rc != QXD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return qxd_fail(ctx, QXD_ECUDA, "MSCG: graph capture failed");
+    }
+    size_t nnodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nnodes);
+    const double it_bytes = (2 * (1952.0 / 96) + 6 + 4 * ns) * (double)hb;  // rough, for the profile only
+    MscgDev* hs = reinterpret_cast<MscgDev*>(ctx->red_host);  // pinned host mirror (large enough)
+    static_assert(sizeof(MscgDev) <= kRedSlots * sizeof(double), "state fits the pinned mirror");
+    while (true) {
+        {
+            ProfScope prof(ctx, "mscg_graph", kGraphIters * it_bytes, st, (int)nnodes);
+            if (cudaGraphLaunch(exec, st) != cudaSuccess) {
+                rc = qxd_fail(ctx, QXD_ECUDA, "MSCG: graph launch failed");
+                break;
+            }
+        }
+        if (cudaMemcpyAsync(hs, dstate, sizeof(MscgDev), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = qxd_fail(ctx, QXD_ECUDA, "MSCG: state read failed");
+            break;
+        }
+        *iters = hs->iter;
+        if (!std::isfinite(hs->rr)) {
+            rc = qxd_fail(ctx, QXD_ENAN, "non-finite value in MSCG");
+            break;
+        }
+        if (verbose()) std::fprintf(stderr, "[qxd mscg-graph] it %d active %d |r|/|b| %.3e\n", hs->iter, hs->nactive,
+                                    std::sqrt(hs->rr) / hs->bn);
+        if (hs->nactive == 0 || hs->iter >= max_iter || hs->alpha == 0.0) break;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    return rc;
+}
+
 int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solver* s, const void* b64, char* X64,
                qxd_info* info, cudaStream_t st) {
     const size_t n = 12ull * ctx->g.Vh;
@@ -531,7 +718,8 @@ int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solv
         return QXD_OK;
     }
     if (P == QXD_FP64) {
-        QXD_TRY(mscg_core(ctx, fl, 0, ns, sigma, b64, X64, s->nmx, 0.5 * s->tol, &it, st));
+        if (graphs_enabled()) QXD_TRY(mscg_core_graph(ctx, fl, 0, ns, sigma, b64, X64, s->nmx, 0.5 * s->tol, &it, st));
+        else QXD_TRY(mscg_core(ctx, fl, 0, ns, sigma, b64, X64, s->nmx, 0.5 * s->tol, &it, st));
         info->iters += it;
     } else {
         const size_t hbP = half_bytes(ctx, P);
@@ -539,7 +727,12 @@ int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solv
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 107, hbP, &bP));
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 108, hbP * ns, &XP));
         QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, b64, 0.0, 0.0, bP, st));
-        QXD_TRY(mscg_core(ctx, fl, P, ns, sigma, bP, static_cast<char*>(XP), s->nmx, std::max(s->tol, 1e-6), &it, st));
+        if (graphs_enabled())
+            QXD_TRY(mscg_core_graph(ctx, fl, P, ns, sigma, bP, static_cast<char*>(XP), s->nmx, std::max(s->tol, 1e-6),
+                                    &it, st));
+        else
+            QXD_TRY(mscg_core(ctx, fl, P, ns, sigma, bP, static_cast<char*>(XP), s->nmx, std::max(s->tol, 1e-6), &it,
+                              st));
         info->iters += it;
         for (int j = 0; j < ns; ++j)
             QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, static_cast<char*>(XP) + j * hbP, 0.0, 0.0, X64 + j * hb64, st));

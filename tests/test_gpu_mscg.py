@@ -10,7 +10,7 @@ import pytest
 from oracle import ratapprox
 from oracle.dirac import gamma5
 from paper_1908_11673_gb300 import workload
-from tests.gpu_helpers import setup
+from tests.gpu_helpers import relerr, setup
 
 pytestmark = pytest.mark.gpu
 
@@ -72,4 +72,25 @@ def test_smeared_16_4_solve_converges():
     sites = np.random.default_rng(0).choice(op.geom.V, 2000, replace=False)
     r = eta[sites] - op.apply(psi, sites)
     assert np.linalg.norm(r) / np.linalg.norm(eta[sites]) < 1e-9
+    ctx.close()
+
+
+def test_graph_and_host_driven_mscg_agree(monkeypatch):
+    """The CUDA-graph MSCG (device-resident scalars) and the host-driven loop run
+    the same recursion: same iteration count, and solutions that agree to the
+    solver tolerance (the FP32 vector updates round in a different order, and
+    each solution is refined to 1e-10 on its own)."""
+    r = ratapprox.load(GOLDEN)
+    sigma = r.mu ** 2
+    qxd, ctx, op, _, _ = setup((8, 8, 8, 8), 0, (np.pi, 0, 0, 0), qhat=-2, seed=3300)
+    ne = op.geom.V // 2
+    phi = workload.spinor(ne, 3301)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("QXD_GRAPHS", flag)
+        x = np.empty((len(sigma), ne, 4, 3), dtype=np.complex128)
+        info = ctx.solve_multishift(0, sigma, phi, x, tol=1e-10, inner=1)
+        out[flag] = (info.iters, x)
+    assert out["1"][0] == out["0"][0]
+    assert relerr(out["1"][1], out["0"][1]) < 1e-9
     ctx.close()
