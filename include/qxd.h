@@ -161,9 +161,12 @@ int qxd_apply_Dhat_eo(qxd_ctx* ctx, int fl, int prec, int dagger, const void* in
 
 /* Solve D psi = eta on the full lattice (complex128 [nrhs][V][4][3]) to the true
  * relative residual s->tol.  CGNE: even-odd system, CG on Dhat^+ Dhat in FP64,
- * odd sites reconstructed.  FGCR: FP64 defect correction whose inner solves run
- * flexible GCR on Dhat in precision s->inner.  info (may be NULL) receives the
- * report of the last right-hand side (status is the worst over all of them).
+ * odd sites reconstructed, one right-hand side after the other.  FGCR: FP64
+ * defect correction whose inner solves run flexible GCR on Dhat in precision
+ * s->inner; with nrhs > 1 all right-hand sides run in lockstep, every iteration
+ * applying Dhat to the whole batch in one multi-right-hand-side launch
+ * (2 nrhs (nkv + 1) <= 512).  info (may be NULL) receives the report (for a batch:
+ * inner iterations of the slowest right-hand side, true_relres the worst).
  * Returns QXD_ENOCONV if any right-hand side misses the tolerance within nmx. */
 int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* psi, int nrhs,
               qxd_info* info, void* stream);

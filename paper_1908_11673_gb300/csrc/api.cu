@@ -336,6 +336,25 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
     QXD_TRY(qxd_ws(ctx, WS_T7, hb, &xo));
     qxd_info local{};
     int worst = QXD_OK;
+    if (s->kind == QXD_FGCR && nrhs > 1) {
+        // all right-hand sides in lockstep: one multi-RHS operator launch per iteration
+        void *bee, *beo, *bxe, *bxo;
+        QXD_TRY(qxd_ws(ctx, WS_T4, hb * nrhs, &bee));
+        QXD_TRY(qxd_ws(ctx, WS_T5, hb * nrhs, &beo));
+        QXD_TRY(qxd_ws(ctx, WS_T6, hb * nrhs, &bxe));
+        QXD_TRY(qxd_ws(ctx, WS_T7, hb * nrhs, &bxo));
+        QXD_TRY(launch_pack(ctx, 0, din, 1, 0, QXD_FP64, bee, nrhs, st));
+        QXD_TRY(launch_pack(ctx, 0, din, 1, 1, QXD_FP64, beo, nrhs, st));
+        int rc = solve_fgcr_dc_batched(ctx, fl, s, Full{bee, beo}, Full{bxe, bxo}, nrhs, &local, st);
+        local.status = rc;
+        if (info) *info = local;
+        if (rc != QXD_OK && rc != QXD_ENOCONV) return rc;
+        QXD_TRY(launch_unpack(ctx, QXD_FP64, bxe, 0, 0, dout, 1, nrhs, st));
+        QXD_TRY(launch_unpack(ctx, QXD_FP64, bxo, 1, 0, dout, 1, nrhs, st));
+        QXD_TRY(finish_out(ctx, psi, dout, cbytes, host_out, st));
+        QXD_CUDA(ctx, cudaStreamSynchronize(st));
+        return rc;
+    }
     for (int r = 0; r < nrhs; ++r) {
         const char* src = static_cast<const char*>(din) + (size_t)r * ctx->g.V * 12 * 16;
         char* dst = static_cast<char*>(dout) + (size_t)r * ctx->g.V * 12 * 16;

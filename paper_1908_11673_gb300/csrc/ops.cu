@@ -57,10 +57,10 @@ int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out
     return launch_hop(ctx, fl, P, a, st);
 }
 
-int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st) {
-    QXD_TRY(launch_diag(ctx, fl, P, 1, 1, r.o, tmp_o, 1, st));
+int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st, int nrhs) {
+    QXD_TRY(launch_diag(ctx, fl, P, 1, 1, r.o, tmp_o, nrhs, st));
     HopArgs a{};
-    a.nrhs = 1;
+    a.nrhs = nrhs;
     a.pout = 0;
     a.in_nb = tmp_o;
     a.in_self = r.e;
@@ -71,9 +71,10 @@ int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tm
     return launch_hop(ctx, fl, P, a, st);
 }
 
-int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void* x_e, void* x_o, cudaStream_t st) {
+int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void* x_e, void* x_o, cudaStream_t st,
+                       int nrhs) {
     HopArgs a{};
-    a.nrhs = 1;
+    a.nrhs = nrhs;
     a.pout = 1;
     a.in_nb = x_e;
     a.in_self = r_o;

@@ -20,9 +20,10 @@ int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStre
 int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out_e, void* tmp_o, cudaStream_t st,
             int nrhs = 1);
 // b_e = r_e - H_eo A_oo^-1 r_o  (even-odd preconditioned source)
-int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st);
+int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st, int nrhs = 1);
 // x_o = A_oo^-1 (r_o - H_oe x_e)
-int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void* x_e, void* x_o, cudaStream_t st);
+int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void* x_e, void* x_o, cudaStream_t st,
+                       int nrhs = 1);
 // z = M r (identity or the learned preconditioner)
 int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z, cudaStream_t st);
 
@@ -36,6 +37,10 @@ int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, con
 // multi-shift CG: b64 even FP64 field, X64 ns consecutive FP64 even fields (output)
 int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solver* s, const void* b64, char* X64,
                qxd_info* info, cudaStream_t st);
+// FGCR + defect correction for nrhs right-hand sides in lockstep (one multi-RHS
+// operator launch per iteration); eta, x: nrhs consecutive fields per parity
+int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, int nrhs,
+                          qxd_info* info, cudaStream_t st);
 int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                   cudaStream_t st);
 

@@ -2,6 +2,7 @@
 // (CGNE), flexible GCR on Dhat inside FP64 defect correction, and the
 // multi-shift CG of the rational approximation (App. A.2).  Host loops drive
 // the kernels; scalars come back to the host once or twice per iteration.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -772,6 +773,238 @@ int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solv
     info->true_relres = worst;
     if (worst <= s->tol) return QXD_OK;
     return qxd_fail(ctx, QXD_ENOCONV, "MSCG: tolerance not reached within nmx");
+}
+
+}  // namespace qxd
+
+namespace qxd {
+
+// ---- batched FGCR: nrhs right-hand sides in lockstep -------------------------------
+// Vectors of the batch are stored as blocks of nrhs consecutive half-lattice
+// fields, so Dhat is applied to the whole block by one multi-right-hand-side
+// launch pair (links and site-diagonal terms read once).  Each right-hand side
+// has its own GCR scalars and stops independently (a finished one keeps its
+// solution and is no longer updated).
+static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const char* b, char* e, int B,
+                              int max_iter, const std::vector<double>& rtol, std::vector<int>& iters, cudaStream_t st) {
+    const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
+    const size_t n = 12ull * ctx->g.Vh;
+    const size_t hb = half_bytes(ctx, P);
+    void *rv, *tov, *tmpv, *Zv, *Wv;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 130, hb * B, &rv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 131, hb * B, &tov));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 132, hb * B, &tmpv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 133, hb * B * nkv, &Zv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 134, hb * B * nkv, &Wv));
+    char* r = static_cast<char*>(rv);
+    char* Z = static_cast<char*>(Zv);
+    char* W = static_cast<char*>(Wv);
+    auto Zk = [&](int k, int j) { return Z + ((size_t)k * B + j) * hb; };
+    auto Wk = [&](int k, int j) { return W + ((size_t)k * B + j) * hb; };
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb * B, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb * B, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> bn(B), rr(B);
+    std::vector<char> done(B, 0);
+    for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, P, n, b + j * hb, 2 * j, st));
+    QXD_TRY(blas_fetch(ctx, 2 * B, st));
+    for (int j = 0; j < B; ++j) {
+        QXD_TRY(status_of_norm(ctx, ctx->red_host[2 * j + 1], "GCR source"));
+        bn[j] = std::sqrt(ctx->red_host[2 * j]);
+        rr[j] = bn[j] * bn[j];
+        iters[j] = 0;
+        done[j] = bn[j] == 0.0 || rtol[j] >= 1.0;
+    }
+    std::vector<double> Rre((size_t)B * nkv * nkv), Rim((size_t)B * nkv * nkv), are((size_t)B * nkv),
+        aim((size_t)B * nkv), ww((size_t)B * nkv), cre(nkv), cim(nkv);
+    std::vector<const void*> Wc(nkv + 1);
+    int it = 0;
+    auto all_done = [&]() {
+        for (int j = 0; j < B; ++j)
+            if (!done[j]) return false;
+        return true;
+    };
+    while (!all_done() && it < max_iter) {
+        int K = 0;
+        std::vector<char> active(done.begin(), done.end());
+        for (int j = 0; j < B; ++j) active[j] = !done[j];
+        for (int k = 0; k < nkv; ++k) {
+            if (s->precond == QXD_PRECOND_NONE) {
+                QXD_CUDA(ctx, cudaMemcpyAsync(Zk(k, 0), r, hb * B, cudaMemcpyDeviceToDevice, st));
+            } else {
+                for (int j = 0; j < B; ++j)
+                    if (active[j] == 1) QXD_TRY(apply_precond(ctx, fl, P, s->precond, r + j * hb, Zk(k, j), st));
+            }
+            QXD_TRY(op_Dhat(ctx, fl, P, 0, Zk(k, 0), Wk(k, 0), tov, st, B));
+            for (int j = 0; j < B; ++j) {
+                if (active[j] != 1) continue;
+                for (int q = 0; q < k; ++q) Wc[q] = Wk(q, j);
+                Wc[k] = r + j * hb;
+                QXD_TRY(blas_multi_dot(ctx, P, n, k + 1, Wc.data(), Wk(k, j), 2 * (k + 1) * j, st));
+            }
+            QXD_TRY(blas_fetch(ctx, 2 * (k + 1) * B, st));
+            std::vector<double> wr_re(B), wr_im(B);
+            for (int j = 0; j < B; ++j) {
+                if (active[j] != 1) continue;
+                const double* h = ctx->red_host + 2 * (k + 1) * j;
+                for (int q = 0; q < k; ++q) {
+                    const size_t o = ((size_t)j * nkv + q) * nkv + k;
+                    Rre[o] = h[2 * q] / ww[(size_t)j * nkv + q];
+                    Rim[o] = h[2 * q + 1] / ww[(size_t)j * nkv + q];
+                }
+                wr_re[j] = h[2 * k];
+                wr_im[j] = -h[2 * k + 1];
+            }
+            for (int j = 0; j < B; ++j) {
+                if (active[j] != 1) continue;
+                for (int q = 0; q < k; ++q) {
+                    const size_t o = ((size_t)j * nkv + q) * nkv + k;
+                    cre[q] = -Rre[o];
+                    cim[q] = -Rim[o];
+                    Wc[q] = Wk(q, j);
+                }
+                QXD_TRY(blas_multi_axpy_norm(ctx, P, n, k, cre.data(), cim.data(), Wc.data(), Wk(k, j), 2 * j, st));
+            }
+            QXD_TRY(blas_fetch(ctx, 2 * B, st));
+            for (int j = 0; j < B; ++j) {
+                if (active[j] != 1) continue;
+                QXD_TRY(status_of_norm(ctx, ctx->red_host[2 * j + 1], "GCR"));
+                const double w2 = ctx->red_host[2 * j];
+                if (!(w2 > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
+                ww[(size_t)j * nkv + k] = w2;
+                are[(size_t)j * nkv + k] = wr_re[j] / w2;
+                aim[(size_t)j * nkv + k] = wr_im[j] / w2;
+                QXD_TRY(blas_axpby(ctx, P, P, n, -are[(size_t)j * nkv + k], -aim[(size_t)j * nkv + k], Wk(k, j), 1.0,
+                                   0.0, r + j * hb, st));
+                rr[j] -= (wr_re[j] * wr_re[j] + wr_im[j] * wr_im[j]) / w2;
+                iters[j] += 1;
+            }
+            ++it;
+            K = k + 1;
+            bool any = false;
+            for (int j = 0; j < B; ++j) {
+                if (active[j] && rr[j] <= rtol[j] * rtol[j] * bn[j] * bn[j]) active[j] = 2;  // converged in-cycle
+                any = any || active[j] == 1;
+            }
+            if (!any || it >= max_iter) break;
+        }
+        // per right-hand side: back substitution and e += sum_k c_k Z_k over the
+        // steps it took part in (a right-hand side that stopped in-cycle has K_j < K)
+        for (int j = 0; j < B; ++j) {
+            if (done[j]) continue;
+            int Kj = 0;
+            for (int k = 0; k < K; ++k)
+                if (ww[(size_t)j * nkv + k] > 0.0) Kj = k + 1;
+            for (int q = Kj - 1; q >= 0; --q) {
+                double sr = are[(size_t)j * nkv + q], si = aim[(size_t)j * nkv + q];
+                for (int k2 = q + 1; k2 < Kj; ++k2) {
+                    const size_t o = ((size_t)j * nkv + q) * nkv + k2;
+                    sr -= Rre[o] * cre[k2] - Rim[o] * cim[k2];
+                    si -= Rre[o] * cim[k2] + Rim[o] * cre[k2];
+                }
+                cre[q] = sr;
+                cim[q] = si;
+            }
+            for (int k = 0; k < Kj; ++k) Wc[k] = Zk(k, j);
+            if (Kj > 0) QXD_TRY(blas_multi_axpy(ctx, P, P, n, Kj, cre.data(), cim.data(), Wc.data(), e + j * hb, st));
+            for (int k = 0; k < nkv; ++k) ww[(size_t)j * nkv + k] = 0.0;
+            if (active[j] == 2) done[j] = 1;
+        }
+        if (all_done() || it >= max_iter) break;
+        // restart: r = b - Dhat e for the whole block
+        QXD_TRY(op_Dhat(ctx, fl, P, 0, e, static_cast<char*>(tmpv), tov, st, B));
+        QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb * B, cudaMemcpyDeviceToDevice, st));
+        QXD_TRY(blas_axpby(ctx, P, P, n * B, -1.0, 0.0, tmpv, 1.0, 0.0, r, st));
+        for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, P, n, r + j * hb, 2 * j, st));
+        QXD_TRY(blas_fetch(ctx, 2 * B, st));
+        for (int j = 0; j < B; ++j) {
+            if (done[j]) continue;
+            rr[j] = ctx->red_host[2 * j];
+            if (rr[j] <= rtol[j] * rtol[j] * bn[j] * bn[j]) done[j] = 1;
+        }
+    }
+    return QXD_OK;
+}
+
+int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, int B,
+                          qxd_info* info, cudaStream_t st) {
+    const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
+    if (2 * (nkv + 1) * B > kRedSlots)
+        return qxd_fail(ctx, QXD_EARG, "batched FGCR: nrhs * (nkv + 1) must not exceed 256");
+    const size_t n = 12ull * ctx->g.Vh;
+    const int P = s->inner;
+    const size_t hb64 = half_bytes(ctx, QXD_FP64), hbP = half_bytes(ctx, P);
+    void *re, *ro, *bP, *roP, *tP, *eeP, *eoP, *to2;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 140, hb64 * B, &re));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 141, hb64 * B, &ro));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 142, hbP * B, &bP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 143, hbP * B, &roP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 144, hbP * B, &tP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 145, hbP * B, &eeP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 146, hbP * B, &eoP));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 147, hbP * B, &to2));
+    char* E = static_cast<char*>(eeP);
+    std::vector<double> enorm(B), relres(B, 1.0);
+    for (int j = 0; j < B; ++j) {
+        QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(eta.e) + j * hb64, 4 * j, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(eta.o) + j * hb64, 4 * j + 2, st));
+    }
+    QXD_TRY(blas_fetch(ctx, 4 * B, st));
+    for (int j = 0; j < B; ++j) {
+        QXD_TRY(status_of_norm(ctx, ctx->red_host[4 * j + 1] + ctx->red_host[4 * j + 3], "source"));
+        enorm[j] = std::sqrt(ctx->red_host[4 * j] + ctx->red_host[4 * j + 2]);
+    }
+    QXD_CUDA(ctx, cudaMemsetAsync(x.e, 0, hb64 * B, st));
+    QXD_CUDA(ctx, cudaMemsetAsync(x.o, 0, hb64 * B, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(re, eta.e, hb64 * B, cudaMemcpyDeviceToDevice, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(ro, eta.o, hb64 * B, cudaMemcpyDeviceToDevice, st));
+    const double itol = s->inner_tol > 0 ? s->inner_tol : (P == QXD_BF16 ? 5e-3 : (P == QXD_FP32 ? 1e-5 : 1e-10));
+    info->iters = 0;
+    info->restarts = 0;
+    info->op_applies = 0;
+    std::vector<int> its(B, 0);
+    for (int outer = 0; outer < 64; ++outer) {
+        if (outer > 0) {
+            // r = eta - D x for the whole batch (FP64)
+            QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, Full{re, ro}, st, B));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.e, -1.0, 0.0, re, st));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.o, -1.0, 0.0, ro, st));
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(re) + j * hb64, 4 * j, st));
+                QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(ro) + j * hb64, 4 * j + 2, st));
+            }
+            QXD_TRY(blas_fetch(ctx, 4 * B, st));
+            bool all = true;
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(status_of_norm(ctx, ctx->red_host[4 * j + 1] + ctx->red_host[4 * j + 3], "residual"));
+                relres[j] = enorm[j] > 0 ? std::sqrt(ctx->red_host[4 * j] + ctx->red_host[4 * j + 2]) / enorm[j] : 0.0;
+                all = all && relres[j] <= s->tol;
+            }
+            info->op_applies += B;
+            if (verbose()) std::fprintf(stderr, "[qxd dc-batched] outer %d worst relres %.3e\n", outer,
+                                        *std::max_element(relres.begin(), relres.end()));
+            if (all) break;
+            info->restarts += 1;
+        }
+        if (info->iters >= s->nmx) break;
+        QXD_TRY(blas_axpby(ctx, 0, P, n * B, 1.0, 0.0, re, 0.0, 0.0, tP, st));
+        QXD_TRY(blas_axpby(ctx, 0, P, n * B, 1.0, 0.0, ro, 0.0, 0.0, roP, st));
+        QXD_TRY(op_eo_source(ctx, fl, P, Full{tP, roP}, bP, to2, st, B));
+        std::vector<double> rtol(B);
+        for (int j = 0; j < B; ++j) rtol[j] = relres[j] <= s->tol ? 1.0 : std::max(itol, 0.5 * s->tol / relres[j]);
+        QXD_TRY(fgcr_inner_batched(ctx, fl, P, s, static_cast<char*>(bP), E, B, s->nmx - info->iters, rtol, its, st));
+        int mx = 0;
+        for (int j = 0; j < B; ++j) mx = std::max(mx, its[j]);
+        info->iters += mx;
+        info->op_applies += mx * B;
+        QXD_TRY(op_odd_reconstruct(ctx, fl, P, roP, E, eoP, st, B));
+        QXD_TRY(blas_axpby(ctx, P, 0, n * B, 1.0, 0.0, E, 1.0, 0.0, x.e, st));
+        QXD_TRY(blas_axpby(ctx, P, 0, n * B, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+    }
+    double worst = 0.0;
+    for (int j = 0; j < B; ++j) worst = std::max(worst, relres[j]);
+    info->true_relres = worst;
+    if (worst <= s->tol) return QXD_OK;
+    return qxd_fail(ctx, QXD_ENOCONV, "batched FGCR: tolerance not reached within nmx");
 }
 
 }  // namespace qxd
