@@ -264,8 +264,57 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr 
     block_reduce_finish<2 * K>(acc, o);
 }
 
+// <a, b> between two precisions, site by site over whole half-lattice fields
+template <int PA, int PB>
+__global__ void __launch_bounds__(kRedThreads) k_dot_site(int Vh, int nf, const void* __restrict__ a,
+                                                          const void* __restrict__ b, RedOut o) {
+    using CA = typename Prec<PA>::chunk;
+    using CB = typename Prec<PB>::chunk;
+    double v[2] = {0.0, 0.0};
+    float f[2] = {0.f, 0.f};
+    int cnt = 0;
+    const long long total = (long long)Vh * nf;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int fi = (int)(t / Vh), h = (int)(t % Vh);
+        cplx<typename Prec<PA>::real> x[12];
+        cplx<typename Prec<PB>::real> y[12];
+        load_spinor<PA>(static_cast<const CA*>(a) + (size_t)fi * Prec<PA>::nchunk * Vh, Vh, h, x);
+        load_spinor<PB>(static_cast<const CB*>(b) + (size_t)fi * Prec<PB>::nchunk * Vh, Vh, h, y);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const float xr = (float)x[k].re, xi = (float)x[k].im, yr = (float)y[k].re, yi = (float)y[k].im;
+            f[0] = fmaf(xr, yr, fmaf(xi, yi, f[0]));
+            f[1] = fmaf(xr, yi, fmaf(-xi, yr, f[1]));
+        }
+        if (++cnt == 2) {
+            v[0] += f[0];
+            v[1] += f[1];
+            f[0] = f[1] = 0.f;
+            cnt = 0;
+        }
+    }
+    v[0] += f[0];
+    v[1] += f[1];
+    block_reduce_finish<2>(v, o);
+}
+
 int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* b, int slot, cudaStream_t st) {
-    if (pa != pb) return qxd_fail(ctx, QXD_EARG, "blas_dot: precisions must match");
+    if (pa != pb) {
+        const int Vh = ctx->g.Vh;
+        if (pa == 0 || pb == 0 || n % (12ull * Vh) != 0)
+            return qxd_fail(ctx, QXD_EARG, "blas_dot: mixed precision only between FP32 and BF16 whole fields");
+        const int nf = (int)(n / (12ull * Vh));
+        ProfScope prof(ctx, "dot_mixed", (double)n * (eb(pa) + eb(pb)), st);
+        const RedOut o = red_out(ctx, slot);
+        const size_t wpb = kRedThreads;
+        if (pa == 1) k_dot_site<1, 2><<<wave_blocks(ctx, k_dot_site<1, 2>, kRedThreads, wpb, (size_t)Vh * nf),
+                                        kRedThreads, 0, st>>>(Vh, nf, a, b, o);
+        else k_dot_site<2, 1><<<wave_blocks(ctx, k_dot_site<2, 1>, kRedThreads, wpb, (size_t)Vh * nf), kRedThreads,
+                                0, st>>>(Vh, nf, a, b, o);
+        QXD_CUDA(ctx, cudaGetLastError());
+        return QXD_OK;
+    }
     const size_t nc = nchunks(pa, n);
     ProfScope prof(ctx, "dot", (double)n * 2 * eb(pa), st);
     const RedOut o = red_out(ctx, slot);

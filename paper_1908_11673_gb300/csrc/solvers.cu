@@ -188,24 +188,48 @@ int cgnr_inner(qxd_ctx* ctx, int fl, int P, const void* b, void* e, int max_iter
     return QXD_OK;
 }
 
+// Precision of the residual and solution vectors of an inner solve whose
+// operator and Krylov basis are stored in precision P: BF16 storage keeps the
+// residual and the solution in FP32 (bfloat16 rounding, 2^-9, would swamp the
+// recursive residual), FP32 and FP64 use their own precision throughout.
+static int vec_prec(int P) { return P == QXD_BF16 ? QXD_FP32 : P; }
+
+// z = M r: r in precision Pv, z in Pb
+static int precond_into(qxd_ctx* ctx, int fl, int Pv, int Pb, int kind, const void* r, void* z, void* ztmp,
+                        cudaStream_t st) {
+    const size_t n = 12ull * ctx->g.Vh;
+    if (Pv == Pb) return apply_precond(ctx, fl, Pv, kind, r, z, st);
+    if (kind == QXD_PRECOND_NONE) return blas_axpby(ctx, Pv, Pb, n, 1.0, 0.0, r, 0.0, 0.0, z, st);
+    QXD_TRY(apply_precond(ctx, fl, Pv, kind, r, ztmp, st));
+    return blas_axpby(ctx, Pv, Pb, n, 1.0, 0.0, ztmp, 0.0, 0.0, z, st);
+}
+
 int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, void* e, int max_iter,
                double rtol, int* iters, bool* stagnated, cudaStream_t st) {
     *stagnated = false;
+    const int Pb = P, Pv = vec_prec(P);
+    const bool split = Pb != Pv;
     const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
     const size_t n = 12ull * ctx->g.Vh;
-    const size_t hb = half_bytes(ctx, P);
-    void *r, *to, *tmp;
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 20, hb, &r));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 21, hb, &to));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 22, hb, &tmp));
+    const size_t hv = half_bytes(ctx, Pv), hbb = half_bytes(ctx, Pb);
+    void *r, *to, *tmp, *ztmp, *tb;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 20, hv, &r));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 21, hbb, &to));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 22, hbb, &tmp));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 23, hv, &ztmp));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 19, hbb, &tb));
+    // Krylov basis: two blocks of nkv fields
+    void *Zb, *Wb;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 24, hbb * nkv, &Zb));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 25, hbb * nkv, &Wb));
     std::vector<void*> Z(nkv), W(nkv);
     for (int k = 0; k < nkv; ++k) {
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 24 + 2 * k, hb, &Z[k]));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 25 + 2 * k, hb, &W[k]));
+        Z[k] = static_cast<char*>(Zb) + (size_t)k * hbb;
+        W[k] = static_cast<char*>(Wb) + (size_t)k * hbb;
     }
-    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
-    QXD_TRY(blas_norm2(ctx, P, n, b, 0, st));
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hv, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hv, cudaMemcpyDeviceToDevice, st));
+    QXD_TRY(blas_norm2(ctx, Pv, n, b, 0, st));
     QXD_TRY(blas_fetch(ctx, 2, st));
     QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "GCR source"));
     const double bn = std::sqrt(ctx->red_host[0]);
@@ -219,12 +243,14 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
         int K = 0;
         const double rr_cycle = rr;
         for (int k = 0; k < nkv; ++k) {
-            QXD_TRY(apply_precond(ctx, fl, P, s->precond, r, Z[k], st));
-            QXD_TRY(op_Dhat(ctx, fl, P, 0, Z[k], W[k], to, st));
-            // <W_j, w_k> for j < k, and <r, w_k>
+            QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, r, Z[k], ztmp, st));
+            QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Z[k], W[k], to, st));
+            // <W_j, w_k> for j < k and <r, w_k>
             for (int j = 0; j < k; ++j) Wc[j] = W[j];
-            Wc[k] = r;
-            QXD_TRY(blas_multi_dot(ctx, P, n, k + 1, Wc.data(), W[k], 0, st));
+            int nd = k;
+            if (!split) Wc[nd++] = r;
+            if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), W[k], 0, st));
+            if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, r, W[k], 2 * k, st));
             QXD_TRY(blas_fetch(ctx, 2 * (k + 1), st));
             for (int j = 0; j < k; ++j) {
                 Rre[j * nkv + k] = ctx->red_host[2 * j] / ww[j];
@@ -236,7 +262,7 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             const double wr_re = ctx->red_host[2 * k], wr_im = -ctx->red_host[2 * k + 1];
             {
                 std::vector<const void*> Wp(W.begin(), W.begin() + k);
-                QXD_TRY(blas_multi_axpy_norm(ctx, P, n, k, cre.data(), cim.data(), Wp.data(), W[k], 0, st));
+                QXD_TRY(blas_multi_axpy_norm(ctx, Pb, n, k, cre.data(), cim.data(), Wp.data(), W[k], 0, st));
             }
             QXD_TRY(blas_fetch(ctx, 2, st));
             ww[k] = ctx->red_host[0];
@@ -247,7 +273,7 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             if (!(ww[k] > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
             are[k] = wr_re / ww[k];
             aim[k] = wr_im / ww[k];
-            QXD_TRY(blas_axpby(ctx, P, P, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
+            QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
             rr -= (wr_re * wr_re + wr_im * wr_im) / ww[k];
             *iters += 1;
             K = k + 1;
@@ -267,14 +293,23 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             cre[j] = sr;
             cim[j] = si;
         }
-        std::vector<const void*> Zp(Z.begin(), Z.begin() + K);
-        QXD_TRY(blas_multi_axpy(ctx, P, P, n, K, cre.data(), cim.data(), Zp.data(), e, st));
+        if (!split) {
+            std::vector<const void*> Zp(Z.begin(), Z.begin() + K);
+            QXD_TRY(blas_multi_axpy(ctx, Pv, Pv, n, K, cre.data(), cim.data(), Zp.data(), e, st));
+        } else {
+            for (int k = 0; k < K; ++k) QXD_TRY(blas_axpby(ctx, Pb, Pv, n, cre[k], cim[k], Z[k], 1.0, 0.0, e, st));
+        }
         if (!done) {
-            // restart: r = b - Dhat e
-            QXD_TRY(op_Dhat(ctx, fl, P, 0, e, tmp, to, st));
-            QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb, cudaMemcpyDeviceToDevice, st));
-            QXD_TRY(blas_axpby(ctx, P, P, n, -1.0, 0.0, tmp, 1.0, 0.0, r, st));
-            QXD_TRY(blas_norm2(ctx, P, n, r, 0, st));
+            // restart: r = b - Dhat e (through the basis precision)
+            if (split) {
+                QXD_TRY(blas_axpby(ctx, Pv, Pb, n, 1.0, 0.0, e, 0.0, 0.0, tb, st));
+                QXD_TRY(op_Dhat(ctx, fl, Pb, 0, tb, tmp, to, st));
+            } else {
+                QXD_TRY(op_Dhat(ctx, fl, Pb, 0, e, tmp, to, st));
+            }
+            QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hv, cudaMemcpyDeviceToDevice, st));
+            QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -1.0, 0.0, tmp, 1.0, 0.0, r, st));
+            QXD_TRY(blas_norm2(ctx, Pv, n, r, 0, st));
             QXD_TRY(blas_fetch(ctx, 2, st));
             rr = ctx->red_host[0];
             if (rr <= rtol * rtol * bn * bn) done = true;
@@ -293,8 +328,9 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
                   cudaStream_t st) {
     const size_t n = 12ull * ctx->g.Vh;
     const int P = s->inner;
+    const int Pv = vec_prec(P);  // precision of the inner solve's vectors (FP32 for BF16 storage)
     const size_t hb64 = half_bytes(ctx, QXD_FP64);
-    const size_t hbP = half_bytes(ctx, P);
+    const size_t hbP = half_bytes(ctx, Pv);
     void *re, *ro, *t64, *bP, *roP, *tP, *eeP, *eoP, *to2;
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 10, hb64, &re));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 11, hb64, &ro));
@@ -339,9 +375,9 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         }
         if (info->iters >= s->nmx) break;
         // even-odd source in precision P: b = r_e - H_eo A_oo^-1 r_o
-        QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, r.e, 0.0, 0.0, tP, st));
-        QXD_TRY(blas_axpby(ctx, 0, P, n, 1.0, 0.0, r.o, 0.0, 0.0, roP, st));
-        QXD_TRY(op_eo_source(ctx, fl, P, Full{tP, roP}, bP, to2, st));
+        QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.e, 0.0, 0.0, tP, st));
+        QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.o, 0.0, 0.0, roP, st));
+        QXD_TRY(op_eo_source(ctx, fl, Pv, Full{tP, roP}, bP, to2, st));
         int it = 0;
         const double rtol = std::max(itol, 0.5 * s->tol / relres);
         if (!use_cgnr) {
@@ -357,14 +393,14 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
             }
         }
         if (use_cgnr) {
-            QXD_TRY(cgnr_inner(ctx, fl, P, bP, eeP, s->nmx - info->iters, rtol, &it, st));
+            QXD_TRY(cgnr_inner(ctx, fl, Pv, bP, eeP, s->nmx - info->iters, rtol, &it, st));
             info->iters += it;
             info->op_applies += 2 * it + 1;
         }
         // e_o = A_oo^-1 (r_o - H_oe e_e);  x += e
-        QXD_TRY(op_odd_reconstruct(ctx, fl, P, roP, eeP, eoP, st));
-        QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
-        QXD_TRY(blas_axpby(ctx, P, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        QXD_TRY(op_odd_reconstruct(ctx, fl, Pv, roP, eeP, eoP, st));
+        QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
+        QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
     }
     double rr;
     QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
@@ -786,26 +822,33 @@ namespace qxd {
 // has its own GCR scalars and stops independently (a finished one keeps its
 // solution and is no longer updated).
 static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const char* b, char* e, int B,
-                              int max_iter, const std::vector<double>& rtol, std::vector<int>& iters, cudaStream_t st) {
+                              int max_iter, const std::vector<double>& rtol, std::vector<int>& iters, bool* stagnated,
+                              cudaStream_t st) {
+    *stagnated = false;
     const int nkv = s->nkv < 1 ? 1 : (s->nkv > 64 ? 64 : s->nkv);
+    const int Pb = P, Pv = vec_prec(P);
+    const bool split = Pb != Pv;
     const size_t n = 12ull * ctx->g.Vh;
-    const size_t hb = half_bytes(ctx, P);
-    void *rv, *tov, *tmpv, *Zv, *Wv;
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 130, hb * B, &rv));
+    const size_t hb = half_bytes(ctx, Pb), hv = half_bytes(ctx, Pv);
+    void *rv, *tov, *tmpv, *Zv, *Wv, *ztmp, *tbv;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 130, hv * B, &rv));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 131, hb * B, &tov));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 132, hb * B, &tmpv));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 133, hb * B * nkv, &Zv));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 134, hb * B * nkv, &Wv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 135, hv, &ztmp));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 136, hb * B, &tbv));
     char* r = static_cast<char*>(rv);
     char* Z = static_cast<char*>(Zv);
     char* W = static_cast<char*>(Wv);
     auto Zk = [&](int k, int j) { return Z + ((size_t)k * B + j) * hb; };
     auto Wk = [&](int k, int j) { return W + ((size_t)k * B + j) * hb; };
-    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hb * B, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb * B, cudaMemcpyDeviceToDevice, st));
+    auto Rj = [&](int j) { return r + (size_t)j * hv; };
+    QXD_CUDA(ctx, cudaMemsetAsync(e, 0, hv * B, st));
+    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hv * B, cudaMemcpyDeviceToDevice, st));
     std::vector<double> bn(B), rr(B);
     std::vector<char> done(B, 0);
-    for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, P, n, b + j * hb, 2 * j, st));
+    for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, Pv, n, b + j * hv, 2 * j, st));
     QXD_TRY(blas_fetch(ctx, 2 * B, st));
     for (int j = 0; j < B; ++j) {
         QXD_TRY(status_of_norm(ctx, ctx->red_host[2 * j + 1], "GCR source"));
@@ -823,23 +866,29 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
             if (!done[j]) return false;
         return true;
     };
+    std::vector<double> rr_cycle(B);
     while (!all_done() && it < max_iter) {
         int K = 0;
+        for (int j = 0; j < B; ++j) rr_cycle[j] = rr[j];
         std::vector<char> active(done.begin(), done.end());
         for (int j = 0; j < B; ++j) active[j] = !done[j];
         for (int k = 0; k < nkv; ++k) {
-            if (s->precond == QXD_PRECOND_NONE) {
+            if (s->precond == QXD_PRECOND_NONE && !split) {
                 QXD_CUDA(ctx, cudaMemcpyAsync(Zk(k, 0), r, hb * B, cudaMemcpyDeviceToDevice, st));
+            } else if (s->precond == QXD_PRECOND_NONE) {
+                QXD_TRY(blas_axpby(ctx, Pv, Pb, n * B, 1.0, 0.0, r, 0.0, 0.0, Zk(k, 0), st));
             } else {
                 for (int j = 0; j < B; ++j)
-                    if (active[j] == 1) QXD_TRY(apply_precond(ctx, fl, P, s->precond, r + j * hb, Zk(k, j), st));
+                    if (active[j] == 1) QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, Rj(j), Zk(k, j), ztmp, st));
             }
-            QXD_TRY(op_Dhat(ctx, fl, P, 0, Zk(k, 0), Wk(k, 0), tov, st, B));
+            QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Zk(k, 0), Wk(k, 0), tov, st, B));
             for (int j = 0; j < B; ++j) {
                 if (active[j] != 1) continue;
                 for (int q = 0; q < k; ++q) Wc[q] = Wk(q, j);
-                Wc[k] = r + j * hb;
-                QXD_TRY(blas_multi_dot(ctx, P, n, k + 1, Wc.data(), Wk(k, j), 2 * (k + 1) * j, st));
+                int nd = k;
+                if (!split) Wc[nd++] = Rj(j);
+                if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), Wk(k, j), 2 * (k + 1) * j, st));
+                if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, Rj(j), Wk(k, j), 2 * (k + 1) * j + 2 * k, st));
             }
             QXD_TRY(blas_fetch(ctx, 2 * (k + 1) * B, st));
             std::vector<double> wr_re(B), wr_im(B);
@@ -862,7 +911,7 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
                     cim[q] = -Rim[o];
                     Wc[q] = Wk(q, j);
                 }
-                QXD_TRY(blas_multi_axpy_norm(ctx, P, n, k, cre.data(), cim.data(), Wc.data(), Wk(k, j), 2 * j, st));
+                QXD_TRY(blas_multi_axpy_norm(ctx, Pb, n, k, cre.data(), cim.data(), Wc.data(), Wk(k, j), 2 * j, st));
             }
             QXD_TRY(blas_fetch(ctx, 2 * B, st));
             for (int j = 0; j < B; ++j) {
@@ -873,8 +922,8 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
                 ww[(size_t)j * nkv + k] = w2;
                 are[(size_t)j * nkv + k] = wr_re[j] / w2;
                 aim[(size_t)j * nkv + k] = wr_im[j] / w2;
-                QXD_TRY(blas_axpby(ctx, P, P, n, -are[(size_t)j * nkv + k], -aim[(size_t)j * nkv + k], Wk(k, j), 1.0,
-                                   0.0, r + j * hb, st));
+                QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[(size_t)j * nkv + k], -aim[(size_t)j * nkv + k], Wk(k, j), 1.0,
+                                   0.0, Rj(j), st));
                 rr[j] -= (wr_re[j] * wr_re[j] + wr_im[j] * wr_im[j]) / w2;
                 iters[j] += 1;
             }
@@ -904,23 +953,37 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
                 cre[q] = sr;
                 cim[q] = si;
             }
-            for (int k = 0; k < Kj; ++k) Wc[k] = Zk(k, j);
-            if (Kj > 0) QXD_TRY(blas_multi_axpy(ctx, P, P, n, Kj, cre.data(), cim.data(), Wc.data(), e + j * hb, st));
+            if (!split) {
+                for (int k = 0; k < Kj; ++k) Wc[k] = Zk(k, j);
+                if (Kj > 0)
+                    QXD_TRY(blas_multi_axpy(ctx, Pv, Pv, n, Kj, cre.data(), cim.data(), Wc.data(), e + j * hv, st));
+            } else {
+                for (int k = 0; k < Kj; ++k)
+                    QXD_TRY(blas_axpby(ctx, Pb, Pv, n, cre[k], cim[k], Zk(k, j), 1.0, 0.0, e + j * hv, st));
+            }
             for (int k = 0; k < nkv; ++k) ww[(size_t)j * nkv + k] = 0.0;
             if (active[j] == 2) done[j] = 1;
         }
         if (all_done() || it >= max_iter) break;
-        // restart: r = b - Dhat e for the whole block
-        QXD_TRY(op_Dhat(ctx, fl, P, 0, e, static_cast<char*>(tmpv), tov, st, B));
-        QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hb * B, cudaMemcpyDeviceToDevice, st));
-        QXD_TRY(blas_axpby(ctx, P, P, n * B, -1.0, 0.0, tmpv, 1.0, 0.0, r, st));
-        for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, P, n, r + j * hb, 2 * j, st));
+        // restart: r = b - Dhat e for the whole block (through the basis precision)
+        if (split) {
+            QXD_TRY(blas_axpby(ctx, Pv, Pb, n * B, 1.0, 0.0, e, 0.0, 0.0, tbv, st));
+            QXD_TRY(op_Dhat(ctx, fl, Pb, 0, tbv, static_cast<char*>(tmpv), tov, st, B));
+        } else {
+            QXD_TRY(op_Dhat(ctx, fl, Pb, 0, e, static_cast<char*>(tmpv), tov, st, B));
+        }
+        QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hv * B, cudaMemcpyDeviceToDevice, st));
+        QXD_TRY(blas_axpby(ctx, Pb, Pv, n * B, -1.0, 0.0, tmpv, 1.0, 0.0, r, st));
+        for (int j = 0; j < B; ++j) QXD_TRY(blas_norm2(ctx, Pv, n, Rj(j), 2 * j, st));
         QXD_TRY(blas_fetch(ctx, 2 * B, st));
         for (int j = 0; j < B; ++j) {
             if (done[j]) continue;
             rr[j] = ctx->red_host[2 * j];
             if (rr[j] <= rtol[j] * rtol[j] * bn[j] * bn[j]) done[j] = 1;
+            // a whole cycle that removed less than 10% of the residual norm
+            else if (K == nkv && rr[j] > 0.81 * rr_cycle[j]) *stagnated = true;
         }
+        if (*stagnated) return QXD_OK;
     }
     return QXD_OK;
 }
@@ -932,7 +995,8 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
         return qxd_fail(ctx, QXD_EARG, "batched FGCR: nrhs * (nkv + 1) must not exceed 256");
     const size_t n = 12ull * ctx->g.Vh;
     const int P = s->inner;
-    const size_t hb64 = half_bytes(ctx, QXD_FP64), hbP = half_bytes(ctx, P);
+    const int Pv = vec_prec(P);
+    const size_t hb64 = half_bytes(ctx, QXD_FP64), hbP = half_bytes(ctx, Pv);
     void *re, *ro, *bP, *roP, *tP, *eeP, *eoP, *to2;
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 140, hb64 * B, &re));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 141, hb64 * B, &ro));
@@ -962,6 +1026,7 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
     info->restarts = 0;
     info->op_applies = 0;
     std::vector<int> its(B, 0);
+    bool use_cgnr = false;
     for (int outer = 0; outer < 64; ++outer) {
         if (outer > 0) {
             // r = eta - D x for the whole batch (FP64)
@@ -986,19 +1051,41 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
             info->restarts += 1;
         }
         if (info->iters >= s->nmx) break;
-        QXD_TRY(blas_axpby(ctx, 0, P, n * B, 1.0, 0.0, re, 0.0, 0.0, tP, st));
-        QXD_TRY(blas_axpby(ctx, 0, P, n * B, 1.0, 0.0, ro, 0.0, 0.0, roP, st));
-        QXD_TRY(op_eo_source(ctx, fl, P, Full{tP, roP}, bP, to2, st, B));
+        QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, re, 0.0, 0.0, tP, st));
+        QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, ro, 0.0, 0.0, roP, st));
+        QXD_TRY(op_eo_source(ctx, fl, Pv, Full{tP, roP}, bP, to2, st, B));
         std::vector<double> rtol(B);
         for (int j = 0; j < B; ++j) rtol[j] = relres[j] <= s->tol ? 1.0 : std::max(itol, 0.5 * s->tol / relres[j]);
-        QXD_TRY(fgcr_inner_batched(ctx, fl, P, s, static_cast<char*>(bP), E, B, s->nmx - info->iters, rtol, its, st));
         int mx = 0;
-        for (int j = 0; j < B; ++j) mx = std::max(mx, its[j]);
+        if (!use_cgnr) {
+            bool stag = false;
+            QXD_TRY(fgcr_inner_batched(ctx, fl, P, s, static_cast<char*>(bP), E, B, s->nmx - info->iters, rtol, its,
+                                       &stag, st));
+            for (int j = 0; j < B; ++j) mx = std::max(mx, its[j]);
+            if (stag) {
+                // restarted GCR stalls on this operator: from here on CG on the normal
+                // equations (FP32 or FP64) for each right-hand side, starting again from 0
+                use_cgnr = true;
+                if (verbose()) std::fprintf(stderr, "[qxd dc-batched] GCR stagnated: CGNR inner\n");
+            }
+        }
+        if (use_cgnr) {
+            for (int j = 0; j < B; ++j) {
+                int it = 0;
+                if (rtol[j] >= 1.0) {
+                    QXD_CUDA(ctx, cudaMemsetAsync(E + j * hbP, 0, hbP, st));
+                    continue;
+                }
+                QXD_TRY(cgnr_inner(ctx, fl, Pv, static_cast<char*>(bP) + j * hbP, E + j * hbP, s->nmx - info->iters,
+                                   rtol[j], &it, st));
+                mx = std::max(mx, 2 * it);
+            }
+        }
         info->iters += mx;
         info->op_applies += mx * B;
-        QXD_TRY(op_odd_reconstruct(ctx, fl, P, roP, E, eoP, st, B));
-        QXD_TRY(blas_axpby(ctx, P, 0, n * B, 1.0, 0.0, E, 1.0, 0.0, x.e, st));
-        QXD_TRY(blas_axpby(ctx, P, 0, n * B, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        QXD_TRY(op_odd_reconstruct(ctx, fl, Pv, roP, E, eoP, st, B));
+        QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, E, 1.0, 0.0, x.e, st));
+        QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
     }
     double worst = 0.0;
     for (int j = 0; j < B; ++j) worst = std::max(worst, relres[j]);
