@@ -313,8 +313,9 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             QXD_TRY(blas_fetch(ctx, 2, st));
             rr = ctx->red_host[0];
             if (rr <= rtol * rtol * bn * bn) done = true;
-            // a whole cycle that removed less than 10% of the residual norm
-            if (!done && K == nkv && rr > 0.81 * rr_cycle) {
+            // a whole cycle that did not halve the residual norm: restarted GCR
+            // stalls (much slower than CG on the normal equations would be)
+            if (!done && K == nkv && rr > 0.25 * rr_cycle) {
                 *stagnated = true;
                 return QXD_OK;
             }
@@ -980,8 +981,8 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
             if (done[j]) continue;
             rr[j] = ctx->red_host[2 * j];
             if (rr[j] <= rtol[j] * rtol[j] * bn[j] * bn[j]) done[j] = 1;
-            // a whole cycle that removed less than 10% of the residual norm
-            else if (K == nkv && rr[j] > 0.81 * rr_cycle[j]) *stagnated = true;
+            // a whole cycle that did not halve the residual norm
+            else if (K == nkv && rr[j] > 0.25 * rr_cycle[j]) *stagnated = true;
         }
         if (*stagnated) return QXD_OK;
     }
