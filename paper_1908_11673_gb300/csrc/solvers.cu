@@ -394,7 +394,9 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
             }
         }
         if (use_cgnr) {
-            QXD_TRY(cgnr_inner(ctx, fl, Pv, bP, eeP, s->nmx - info->iters, rtol, &it, st));
+            // CGNR runs in the vector precision (FP32 for BF16 storage): it can go to 1e-5
+            const double ctol = Pv == QXD_FP64 ? rtol : std::max(1e-5, 0.5 * s->tol / relres);
+            QXD_TRY(cgnr_inner(ctx, fl, Pv, bP, eeP, s->nmx - info->iters, ctol, &it, st));
             info->iters += it;
             info->op_applies += 2 * it + 1;
         }
@@ -1077,8 +1079,9 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
                     QXD_CUDA(ctx, cudaMemsetAsync(E + j * hbP, 0, hbP, st));
                     continue;
                 }
+                const double ctol = Pv == QXD_FP64 ? rtol[j] : std::max(1e-5, 0.5 * s->tol / relres[j]);
                 QXD_TRY(cgnr_inner(ctx, fl, Pv, static_cast<char*>(bP) + j * hbP, E + j * hbP, s->nmx - info->iters,
-                                   rtol[j], &it, st));
+                                   ctol, &it, st));
                 mx = std::max(mx, 2 * it);
             }
         }
