@@ -16,6 +16,7 @@
 // result is the same on every run.
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "blas.h"
 #include "qxd_internal.h"
@@ -404,38 +405,45 @@ __global__ void k_axpby(size_t nch, double ar, double ai, const void* __restrict
     }
 }
 
-// y = a*x + b*y between two precisions, site by site
+// y = a*x + b*y between two precisions, site by site (grid: sites x fields)
 template <int PX, int PY>
-__global__ void k_axpby_site(int Vh, int nfields, double ar, double ai, const void* __restrict__ x, double br,
-                             double bi, void* __restrict__ y) {
+__global__ void k_axpby_site(int Vh, double ar, double ai, const void* __restrict__ x, double br, double bi,
+                             void* __restrict__ y) {
     using RX = typename Prec<PX>::real;
     using RY = typename Prec<PY>::real;
     using CX = typename Prec<PX>::chunk;
     using CY = typename Prec<PY>::chunk;
-    const bool useb = !(br == 0.0 && bi == 0.0);
-    const long long total = (long long)Vh * nfields;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int f = (int)(t / Vh), h = (int)(t % Vh);
-        const CX* xb = static_cast<const CX*>(x) + (size_t)f * Prec<PX>::nchunk * Vh;
-        CY* yb = static_cast<CY*>(y) + (size_t)f * Prec<PY>::nchunk * Vh;
-        cplx<RX> xs[12];
-        load_spinor<PX>(xb, Vh, h, xs);
-        cplx<RY> ys[12];
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const int f = blockIdx.y;
+    const CX* xb = static_cast<const CX*>(x) + (size_t)f * Prec<PX>::nchunk * Vh;
+    CY* yb = static_cast<CY*>(y) + (size_t)f * Prec<PY>::nchunk * Vh;
+    cplx<RX> xs[12];
+    load_spinor<PX>(xb, Vh, h, xs);
+    cplx<RY> ys[12];
+    const bool copy = ar == 1.0 && ai == 0.0 && br == 0.0 && bi == 0.0;
+    if (copy) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ys[k] = {(RY)xs[k].re, (RY)xs[k].im};
+    } else {
+        const bool useb = !(br == 0.0 && bi == 0.0);
         if (useb) load_spinor<PY>(yb, Vh, h, ys);
+        // the wider of the two precisions carries the arithmetic
+        using RW = typename std::conditional<(sizeof(RX) > sizeof(RY)), RX, RY>::type;
+        const RW a_r = (RW)ar, a_i = (RW)ai, b_r = (RW)br, b_i = (RW)bi;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-            const double xr = xs[k].re, xi = xs[k].im;
-            double r = ar * xr - ai * xi, i = ar * xi + ai * xr;
+            const RW xr = xs[k].re, xi = xs[k].im;
+            RW r = a_r * xr - a_i * xi, i = a_r * xi + a_i * xr;
             if (useb) {
-                const double yr = ys[k].re, yi = ys[k].im;
-                r += br * yr - bi * yi;
-                i += br * yi + bi * yr;
+                const RW yr = ys[k].re, yi = ys[k].im;
+                r += b_r * yr - b_i * yi;
+                i += b_r * yi + b_i * yr;
             }
             ys[k] = {(RY)r, (RY)i};
         }
-        store_spinor<PY>(yb, Vh, h, ys);
     }
+    store_spinor<PY>(yb, Vh, h, ys);
 }
 
 // y += sum_j c_j X_j (same precision); with NORM also |y|^2 of the result
@@ -494,8 +502,8 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
         const int Vh = ctx->g.Vh;
         if (n % (12ull * Vh) != 0) return qxd_fail(ctx, QXD_EARG, "blas_axpby: mixed precision needs whole fields");
         const int nf = (int)(n / (12ull * Vh));
-        const int nb = upd_blocks(ctx, (size_t)Vh * nf);
-#define QXD_AXPBY(A, B) k_axpby_site<A, B><<<nb, 256, 0, st>>>(Vh, nf, ar, ai, x, br, bi, y)
+        const dim3 grid(nblocks(Vh, 128), nf);
+#define QXD_AXPBY(A, B) k_axpby_site<A, B><<<grid, 128, 0, st>>>(Vh, ar, ai, x, br, bi, y)
         if (px == 0 && py == 1) QXD_AXPBY(0, 1);
         else if (px == 1 && py == 0) QXD_AXPBY(1, 0);
         else if (px == 0 && py == 2) QXD_AXPBY(0, 2);
