@@ -47,6 +47,12 @@ FLOP_PER_SITE = 2112
 FP64_PEAK_TFLOPS = 1.19
 
 
+# DRAM bytes per output site measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# on the 24^3x48 lattice for the current kernels (profiles/k_hop_mr_traffic_24x24x24x48.md);
+# a launch on another lattice moves these bytes times its V/2 sites.
+NCU_BYTES_PER_SITE = {"hop_fp32_self1_post0": 1000.6, "hop_fp32_self0_post1": 898.4}
+
+
 def hop_bytes_per_launch(entry, V):
     """Algorithmic bytes of one FP64 hopping launch without right-hand-side scaling
     (used to recover the number of right-hand sides of a profile entry)."""
@@ -314,9 +320,12 @@ def run_native(args, w, name):
                     "hbm_GBps": bytes_per_launch / (mean_ms * 1e-3) / 1e9, "traffic": None}
     else:
         achieved = bytes_per_launch / (mean_ms * 1e-3) / 1e9
+        per_site = NCU_BYTES_PER_SITE.get(dom["name"])
         roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (HBM copy bandwidth)",
-                    "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_ms, "traffic": None}
+                    "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_ms,
+                    "traffic": per_site * (V // 2) if per_site else None,
+                    "traffic_source": "ncu dram bytes per site on 24^3x48 scaled to this lattice" if per_site else None}
     kernels = []
     for p in sorted(prof, key=lambda p: -p["ms"]):
         gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None
