@@ -62,7 +62,7 @@ typedef enum { QXD_FP64 = 0, QXD_FP32 = 1, QXD_BF16 = 2 } qxd_prec;
 
 typedef enum { QXD_CGNE = 0, QXD_FGCR = 1, QXD_MSCG = 2 } qxd_solver_kind;
 
-typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1 } qxd_precond_kind;
+typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1, QXD_PRECOND_SAP = 2 } qxd_precond_kind;
 
 /* Geometry (Sec. 2.1).  Every L[mu] must be even and >= 2.
  * cstar in 0..3: C* boundary conditions in directions 1..cstar.
@@ -99,7 +99,9 @@ typedef struct {
  *          QXD_FP64 makes FGCR a plain FP64 solver).
  * inner_tol : relative residual reduction requested from each inner solve
  *          (0 selects 1e-5 for FP32 and 5e-3 for BF16 storage).
- * precond: right preconditioner of FGCR (QXD_PRECOND_NONE or QXD_PRECOND_LEARNED). */
+ * precond: right preconditioner of FGCR: QXD_PRECOND_NONE, QXD_PRECOND_LEARNED (the network of
+ *          qxd_set_precond_weights) or QXD_PRECOND_SAP (Schwarz alternating procedure, see
+ *          qxd_set_sap; needs every simulated extent to be a multiple of 4). */
 typedef struct {
     int kind;
     double tol;
@@ -212,6 +214,21 @@ int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dagger, const 
  * [cout][cin][9][4][4] spin matrices (interleaved re, im), layers one after the
  * other.  The network is not part of the paper. */
 int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch);
+
+/* ---- SAP preconditioner (Sec. 4.1 and 4.4: SAP+GCR) ----
+ * Blocks of 4^4 sites coloured like a checkerboard; one application M eta runs
+ * ncy cycles over the two colours, each block solving its Dirichlet block system
+ * (hops leaving the block dropped) approximately by nmr minimal-residual steps on
+ * the block's even-odd system, with the full residual rho = eta - D psi refreshed
+ * after every colour.  FGCR on Dhat uses z_e = (M (r_e, 0))_e (Dhat^-1 = (D^-1)_ee).
+ * Arithmetic in FP32. */
+
+/* Set ncy and nmr (1..64 each; default 5 and 5, the paper's values). */
+int qxd_set_sap(qxd_ctx* ctx, int ncy, int nmr);
+
+/* out = M in on the full lattice, complex64 [V][4][3] (host or device arrays).
+ * QXD_EARG unless every simulated extent is a multiple of 4.  Synchronises `stream`. */
+int qxd_sap_apply(qxd_ctx* ctx, int fl, const void* in, void* out, void* stream);
 
 /* ---- learned preconditioner: inference and training (not part of the paper) ----
  * The network M and its weight layout are those of qxd_set_precond_weights.

@@ -320,6 +320,8 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
         return qxd_fail(ctx, QXD_EARG, "solve: inner precision must be 0, 1 or 2");
     if (s->precond == QXD_PRECOND_LEARNED && !ctx->fl[fl].W)
         return qxd_fail(ctx, QXD_ESTATE, "solve: learned preconditioner weights not set");
+    if (s->precond < 0 || s->precond > QXD_PRECOND_SAP) return qxd_fail(ctx, QXD_EARG, "solve: unknown preconditioner");
+    if (s->precond == QXD_PRECOND_SAP) QXD_TRY(sap_check(ctx));
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cbytes = (size_t)nrhs * ctx->g.V * 12 * 16;

@@ -31,6 +31,10 @@ int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z,
 int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const void* r_e, void* z_e,
                        cudaStream_t st);
 
+// SAP preconditioner (sap.cu): z_e = (M_SAP (r_e, 0))_e on FP32 internal even fields
+int sap_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st);
+int sap_check(qxd_ctx* ctx);
+
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                  cudaStream_t st);

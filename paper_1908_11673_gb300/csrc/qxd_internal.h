@@ -64,6 +64,7 @@ struct qxd_ctx {
     // keyed by (precision, self mode, post mode, nrhs, V/2)
     std::map<std::tuple<int, int, int, int, long long>, std::pair<int, int>> tune_hop;
     cudaStream_t cap_stream = nullptr;  // library stream for CUDA-graph capture
+    int sap_ncy = 5, sap_nmr = 5;       // SAP preconditioner parameters (qxd_set_sap)
 };
 
 // Brackets one kernel launch when profiling is on: counts it under `name` with

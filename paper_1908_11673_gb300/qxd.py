@@ -18,14 +18,14 @@ LIBPATH = os.path.join(HERE, "libqxd.so")
 
 FP64, FP32, BF16 = 0, 1, 2
 CGNE, FGCR, MSCG = 0, 1, 2
-PRECOND_NONE, PRECOND_LEARNED = 0, 1
+PRECOND_NONE, PRECOND_LEARNED, PRECOND_SAP = 0, 1, 2
 
 STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: "QXD_ENAN",
           5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
 
 EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_apply_Dw",
            "qxd_apply_Dhat_eo", "qxd_apply_Dhat_eo_noalloc", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
-           "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
+           "qxd_set_sap", "qxd_sap_apply", "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -80,6 +80,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_solve": (i, [vp, i, ctypes.POINTER(Solver), vp, vp, i, ctypes.POINTER(Info), vp]),
         "qxd_solve_multishift": (i, [vp, i, i, vp, ctypes.POINTER(Solver), vp, vp, ctypes.POINTER(Info), vp]),
         "qxd_set_precond_weights": (i, [vp, i, vp, i, i]),
+        "qxd_set_sap": (i, [vp, i, i]),
+        "qxd_sap_apply": (i, [vp, i, vp, vp, vp]),
         "qxd_ptc_apply": (i, [vp, i, vp, i, i, vp, vp, vp]),
         "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(d), vp, vp]),
         "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, ctypes.POINTER(i), vp, vp]),
@@ -202,6 +204,13 @@ class Context:
         if check:
             self._check(rc)
         return info
+
+    # ---- SAP preconditioner ----------------------------------------------------
+    def set_sap(self, ncy=5, nmr=5):
+        self._check(self.lib.qxd_set_sap(self._h, int(ncy), int(nmr)))
+
+    def sap_apply(self, fl, inp, out, stream=None):
+        self._check(self.lib.qxd_sap_apply(self._h, int(fl), _ptr(inp), _ptr(out), _stream(stream)))
 
     # ---- learned preconditioner ------------------------------------------------
     def ptc_apply(self, fl, W, nlayers, nch, inp, out, stream=None):
