@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(kSapThreads) k_sap_block(Geo g, SapDev a, int 
 
 int sap_check(qxd_ctx* ctx) {
     for (int mu = 0; mu < 4; ++mu)
-        if (ctx->g.N[mu] % kSapB)
-            return qxd_fail(ctx, QXD_EARG, "SAP: every simulated extent must be a multiple of 4");
+        if (ctx->g.N[mu] % kSapB || ctx->g.N[mu] < 2 * kSapB)
+            return qxd_fail(ctx, QXD_EARG, "SAP: every simulated extent must be a multiple of 4 and at least 8");
     return QXD_OK;
 }
 
@@ -249,8 +249,8 @@ int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStr
     const size_t hb = half_bytes(ctx, QXD_FP32);
     const size_t n2 = 24ull * g.Vh;  // complex numbers of a full field
     void *rho, *dpsi;
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 60, 2 * hb, &rho));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 61, 2 * hb, &dpsi));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 0, 2 * hb, &rho));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 1, 2 * hb, &dpsi));
     const QxdFlavour& F = ctx->fl[fl];
     SapDev a;
     int nblk = 1;
@@ -293,8 +293,8 @@ int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStr
 int sap_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st) {
     const size_t hb = half_bytes(ctx, QXD_FP32);
     void *eta, *psi;
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 62, 2 * hb, &eta));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 63, 2 * hb, &psi));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 2, 2 * hb, &eta));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 3, 2 * hb, &psi));
     QXD_CUDA(ctx, cudaMemcpyAsync(eta, r_e, hb, cudaMemcpyDeviceToDevice, st));
     QXD_CUDA(ctx, cudaMemsetAsync(static_cast<char*>(eta) + hb, 0, hb, st));
     QXD_TRY(sap_apply_full(ctx, fl, static_cast<const float4*>(eta), static_cast<float4*>(psi), st));
@@ -327,10 +327,10 @@ int qxd_sap_apply(qxd_ctx* ctx, int fl, const void* in, void* out, void* stream)
     const size_t cb = (size_t)ctx->g.V * 12 * 8;
     const size_t hb = half_bytes(ctx, QXD_FP32);
     void *cin, *cout, *fin, *fout;
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 64, cb, &cin));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 65, cb, &cout));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 66, 2 * hb, &fin));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 67, 2 * hb, &fout));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 4, cb, &cin));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 5, cb, &cout));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 6, 2 * hb, &fin));
+    QXD_TRY(qxd_ws(ctx, WS_SAP + 7, 2 * hb, &fout));
     QXD_CUDA(ctx, cudaMemcpyAsync(cin, in, cb, cudaMemcpyDefault, st));
     char* fi = static_cast<char*>(fin);
     char* fo = static_cast<char*>(fout);

@@ -15,7 +15,7 @@ def block_matrix_dense(op, sap):
     return D * (blk[:, None] == blk[None, :])
 
 
-@pytest.mark.parametrize("L,cstar", [((4, 4, 2, 4), 0), ((2, 4, 2, 4), 1)])
+@pytest.mark.parametrize("L,cstar", [((4, 4, 4, 4), 0), ((4, 2, 4, 4), 1)])
 def test_block_operator_is_D_without_cross_block_hops(L, cstar):
     op, _, _ = make_op(L, cstar, (np.pi, 0, 0, 0), qhat=4, seed=12, kappa=0.13)
     sap = SAP(op, bsize=2)
@@ -27,7 +27,7 @@ def test_block_operator_is_D_without_cross_block_hops(L, cstar):
 
 
 def test_block_minres_converges_to_the_block_inverse():
-    op, _, _ = make_op((4, 4, 2, 4), 0, (np.pi, 0, 0, 0), qhat=-2, seed=13, kappa=0.125)
+    op, _, _ = make_op((4, 4, 4, 4), 0, (np.pi, 0, 0, 0), qhat=-2, seed=13, kappa=0.125)
     sap = SAP(op, bsize=2, nmr=200)
     DB = block_matrix_dense(op, sap)
     rho = workload.spinor(op.geom.V, 2)
@@ -40,13 +40,20 @@ def test_block_minres_converges_to_the_block_inverse():
 
 
 def test_sap_iteration_converges_to_the_solution():
-    op, _, _ = make_op((4, 4, 2, 4), 0, (np.pi, 0, 0, 0), qhat=-2, seed=14, kappa=0.12)
+    op, _, _ = make_op((4, 4, 4, 4), 0, (np.pi, 0, 0, 0), qhat=-2, seed=14, kappa=0.12)
     V = op.geom.V
     eta = workload.spinor(V, 3)
     D = dense(lambda v: op.apply(v), V * 12, (V, 4, 3))
     x = np.linalg.solve(D, eta.reshape(-1)).reshape(V, 4, 3)
     errs = [np.linalg.norm(SAP(op, bsize=2, ncy=c, nmr=8).apply(eta) - x) / np.linalg.norm(x) for c in (1, 3, 8)]
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3, errs
+
+
+@pytest.mark.parametrize("L", [(2, 4, 4, 4), (4, 4, 6, 4)])
+def test_sap_needs_two_blocks_per_direction(L):
+    op, _, _ = make_op(L, 0, (np.pi, 0, 0, 0))
+    with pytest.raises(ValueError):
+        SAP(op, bsize=2 if L[2] == 4 else 4)
 
 
 def test_sap_is_gauge_covariant():
