@@ -19,7 +19,12 @@ Reported:
              CUDA-event duration, against the measured HBM copy bandwidth;
   e2e        the same metric through the C ABI with pinned HOST buffers (the
              library copies eta in and psi out inside the timed call);
-  cpu_baseline  the FP64 oracle applying D_w to a bounded sample of sites.
+  cpu_baseline  the FP64 oracle applying D_w to a bounded sample of sites;
+  next_rows  outside the timed region, on the same system: the SAP-preconditioned
+             solve (Sec. 4.4 SAP+GCR) against the unpreconditioned one, and the
+             pseudofermion action of the printed degree-10 rational approximation
+             (App. A.2: one 10-shift multi-shift CG plus FP64 assembly) and the
+             small-determinant action (Sec. 2.2), each timed with CUDA events.
 
 --impl reference times the oracle (the plain CPU implementation) on the same
 metric, each step a bounded sample of sites of the same workload.
@@ -51,6 +56,28 @@ FP64_PEAK_TFLOPS = 1.19
 # on the 24^3x48 lattice for the current kernels (profiles/k_hop_mr_traffic_24x24x24x48.md);
 # a launch on another lattice moves these bytes times its V/2 sites.
 NCU_BYTES_PER_SITE = {"hop_fp32_self1_post0": 1000.6, "hop_fp32_self0_post1": 898.4}
+
+
+GOLDEN_RATIONAL = os.path.join(ROOT, "tests", "golden", "rational_deg10_pow_m1_4.txt")
+
+
+def read_rational(path):
+    """(A, nu[], mu[]) from a [Rational] record (key value lines, '#' comments)."""
+    vals, nu, mu = {}, {}, {}
+    with open(path) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line or line.startswith("["):
+                continue
+            key, *rest = line.split()
+            if key.startswith("nu["):
+                nu[int(key[3:-1])] = float(rest[0])
+            elif key.startswith("mu["):
+                mu[int(key[3:-1])] = float(rest[0])
+            else:
+                vals[key] = rest
+    n = int(vals["degree"][0])
+    return float(vals["A"][0]), np.array([nu[i] for i in range(n)]), np.array([mu[i] for i in range(n)])
 
 
 def hop_bytes_per_launch(entry, V):
@@ -293,6 +320,35 @@ def run_native(args, w, name):
                                               stream=stream), 1)
         base = {"fp64_cgne_ms": ms64, "iters": inf64[0].iters, "true_relres": inf64[0].true_relres}
 
+    # ---- next rows of the method on the same system (not part of the timed step) --------
+    nxt = None
+    if not args.no_extras:
+        nxt = {}
+        for ncy, nmr in ((5, 5), (3, 4)):
+            ctx.set_sap(ncy, nmr)
+            ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP, "nkv": 16}))
+            ctx.profile(2)
+            ms_sap, inf_sap = timed(lambda: ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP,
+                                                                                      "nkv": 16})), 1)
+            ps = {p["name"]: p for p in ctx.profile_entries()}
+            ctx.profile(0)
+            blk = ps.get("sap_block")
+            nxt[f"sap_fgcr_ncy{ncy}_nmr{nmr}"] = {
+                "ms": ms_sap, "iters": inf_sap[0].iters, "true_relres": inf_sap[0].true_relres,
+                "sap_block_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
+                "sap_block_launches": blk["launches"] if blk else None}
+        A_r, nu_r, mu_r = read_rational(GOLDEN_RATIONAL)
+        rat = qxd.rational(A_r, nu_r, mu_r)
+        phi_e = torch.from_numpy(np.ascontiguousarray(eta[: V // 2])).to(dev)
+        ctx.pf_action(0, rat, 0, 9, phi_e, tol=1e-10, stream=stream)
+        ms_pf, _ = timed(lambda: ctx.pf_action(0, rat, 0, 9, phi_e, tol=1e-10, stream=stream), 1)
+        S_pf, inf_pf = ctx.pf_action(0, rat, 0, 9, phi_e, tol=1e-10, stream=stream)
+        nxt["pf_action_deg10"] = {"ms": ms_pf, "S_over_phi2": S_pf / float(np.vdot(eta[: V // 2], eta[: V // 2]).real),
+                                  "cg_iters": inf_pf.iters, "worst_shift_relres": inf_pf.true_relres}
+        ctx.sdet(0, stream=stream)
+        ms_sd, _ = timed(lambda: ctx.sdet(0, stream=stream), 3)
+        nxt["sdet"] = {"ms": ms_sd / 3, "logdet_per_odd_site": ctx.sdet(0, stream=stream)[0] / (V // 2)}
+
     # ---- aggregate over ranks ----------------------------------------------------------
     total_value = value_rank
     if dist:
@@ -361,6 +417,7 @@ def run_native(args, w, name):
         "setup_s": setup_s,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "next_rows": nxt,
     }
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -378,6 +435,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="32^3x64-cstar3")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the SAP and rational-function measurements")
     ap.add_argument("--nmx", type=int, default=100000,
                     help="operator applications per solve; below 100000 a solve that stops early is reported, "
                          "not raised (profiler captures)")

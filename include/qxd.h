@@ -101,7 +101,7 @@ typedef struct {
  *          (0 selects 1e-5 for FP32 and 5e-3 for BF16 storage).
  * precond: right preconditioner of FGCR: QXD_PRECOND_NONE, QXD_PRECOND_LEARNED (the network of
  *          qxd_set_precond_weights) or QXD_PRECOND_SAP (Schwarz alternating procedure, see
- *          qxd_set_sap; needs every simulated extent to be a multiple of 4). */
+ *          qxd_set_sap; needs every simulated extent to be a multiple of 4 and at least 8). */
 typedef struct {
     int kind;
     double tol;
@@ -181,6 +181,63 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
 int qxd_solve_multishift(qxd_ctx* ctx, int fl, int nshift, const double* sigma, const qxd_solver* s,
                          const void* phi_e, void* x_e, qxd_info* info, void* stream);
 
+/* Rational approximation of order [n, n] in q2 (App. A.1, eq. ratfunc):
+ *   rho(q2) = A prod_{j=0..n-1} (q2 + nu[j]^2) / (q2 + mu[j]^2),   1 <= n <= 32.
+ * The coefficients are inputs: the paper obtains them from a separate minmax
+ * program.  Factor ranges k..l below are 0-based and inclusive (the paper's
+ * j = k+1 .. l+1).  The mu[j]^2 of a factor must be pairwise distinct. */
+typedef struct {
+    int n;
+    double A;
+    const double* nu;
+    const double* mu;
+} qxd_rational;
+
+/* out_e = P_{k,l} in_e with P_{k,l} = prod_{j=k..l} (Q2 + nu_j^2) / (Q2 + mu_j^2),
+ * Q2 = Dhat^+ Dhat (App. A.2, eq. Pfactor), evaluated through its partial fractions
+ * P_{k,l} = 1 + sum_j sigma_j (Q2 + mu_j^2)^-1 with one multi-shift CG (solver
+ * parameters as in qxd_solve_multishift: each shift to relative residual s->tol).
+ * in_e, out_e: complex128 [V/2][4][3], host or device; the full R = A P_{0,n-1}.
+ * info (may be NULL): CG iterations and the worst shift residual. */
+int qxd_rat_apply(qxd_ctx* ctx, int fl, const qxd_rational* r, int k, int l, const qxd_solver* s,
+                  const void* in_e, void* out_e, qxd_info* info, void* stream);
+
+/* Pseudofermion action of the factor P_{k,l} (App. A.2, eqs. Spf, Spf2):
+ * *S = (phi, phi) + sum_{j=k..l} sigma_j (phi, (Q2 + mu_j^2)^-1 phi) = (phi, P_{k,l} phi),
+ * phi_e complex128 [V/2][4][3] (host or device), sums in FP64. */
+int qxd_pf_action(qxd_ctx* ctx, int fl, const qxd_rational* r, int k, int l, const qxd_solver* s,
+                  const void* phi_e, double* S, qxd_info* info, void* stream);
+
+/* Stochastic estimate of the reweighting factor W_rat = det[Q2^alpha R] with
+ * alpha = u/v (App. A.3, eqs. Wrat2, Wrat3): Z = Q2^u R^v - 1, R = A P_{0,n-1};
+ * terms[i] = (eta, Z^(i+1) eta) for i < nterms (1..16), and *exponent (may be NULL)
+ * = sum_i c_{v,i+1} terms[i], c_{v,n} the Taylor coefficients of (1 + Z)^(-1/v);
+ * one source eta gives the estimate exp(-*exponent).  Each power of Z costs v
+ * multi-shift solves and u applications of Q2. */
+int qxd_rw_rat(qxd_ctx* ctx, int fl, const qxd_rational* r, int u, int v, int nterms, const qxd_solver* s,
+               const void* eta_e, double* terms, double* exponent, qxd_info* info, void* stream);
+
+/* Exponent of the stochastic estimate of det Ptilde_{k,l}^-1, the factor k..l of
+ * the reweighting factor W_rtm = det[R^-1 R_mu] (App. A.3):
+ *   *exponent = (eta, [Ptilde_{k,l} - 1] eta),
+ *   Ptilde_{k,l} = prod_j (Q2 + mu_j^2)(Q2 + nutilde_j^2) / ((Q2 + nu_j^2)(Q2 + mutilde_j^2)),
+ * with (nu, mu) from r_mu (the approximation of (Q2 + muhat^2)^-alpha) and
+ * (nutilde, mutilde) from r_t (that of Q2^-alpha), both of the same degree;
+ * l - k + 1 <= 16.  Evaluated in the combined form the paper recommends for
+ * stability: sum_j (sigma_j + sigmatilde_j) (eta, x_j)
+ * + sigmatilde_j (nu_j^2 - mutilde_j^2) (x_j, y_j), x_j = (Q2 + nu_j^2)^-1 eta,
+ * y_j = (Q2 + mutilde_j^2)^-1 eta, all from one multi-shift CG. */
+int qxd_rw_rtm(qxd_ctx* ctx, int fl, const qxd_rational* r_mu, const qxd_rational* r_t, int k, int l,
+               const qxd_solver* s, const void* eta_e, double* exponent, qxd_info* info, void* stream);
+
+/* Small-determinant action (Sec. 2.2; det D = det D_oo det Dhat):
+ * *logdet = sum over odd sites x of log |det D_oo(x)|, D_oo(x) = 1/(2 kappa) + dD_sw
+ * (12x12), in FP64 from an LDL^H factorisation of each 6x6 chiral block;
+ * S_sdet = -alpha_f *logdet for a flavour of weight alpha_f.  *nneg (may be NULL)
+ * receives the number of odd sites with a negative determinant.  QXD_ENAN if a
+ * block has a vanishing leading minor.  Synchronises `stream`. */
+int qxd_sdet(qxd_ctx* ctx, int fl, double* logdet, int* nneg, void* stream);
+
 /* Dhat for callers that cannot allocate device memory during the call.  The
  * paper has no counterpart; this is an interface convenience.  Some callers own
  * all device memory through their own pool allocator and have nothing left for
@@ -227,7 +284,8 @@ int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, i
 int qxd_set_sap(qxd_ctx* ctx, int ncy, int nmr);
 
 /* out = M in on the full lattice, complex64 [V][4][3] (host or device arrays).
- * QXD_EARG unless every simulated extent is a multiple of 4.  Synchronises `stream`. */
+ * QXD_EARG unless every simulated extent is a multiple of 4 and at least 8 (two blocks,
+ * so that every block face is a Dirichlet boundary).  Synchronises `stream`. */
 int qxd_sap_apply(qxd_ctx* ctx, int fl, const void* in, void* out, void* stream);
 
 /* ---- learned preconditioner: inference and training (not part of the paper) ----

@@ -94,7 +94,7 @@ static bool is_device_ptr(const void* p) {
 }
 
 // device view of a caller array: the array itself, or a staged copy of it
-static int stage_in(qxd_ctx* ctx, int slot, const void* p, size_t bytes, const void** dev, cudaStream_t st) {
+int stage_in(qxd_ctx* ctx, int slot, const void* p, size_t bytes, const void** dev, cudaStream_t st) {
     if (is_device_ptr(p)) {
         *dev = p;
         return QXD_OK;
@@ -106,7 +106,7 @@ static int stage_in(qxd_ctx* ctx, int slot, const void* p, size_t bytes, const v
     return QXD_OK;
 }
 
-static int stage_out(qxd_ctx* ctx, int slot, void* p, size_t bytes, void** dev, bool* host) {
+int stage_out(qxd_ctx* ctx, int slot, void* p, size_t bytes, void** dev, bool* host) {
     *host = !is_device_ptr(p);
     if (!*host) {
         *dev = p;
@@ -115,7 +115,7 @@ static int stage_out(qxd_ctx* ctx, int slot, void* p, size_t bytes, void** dev, 
     return qxd_ws(ctx, slot, bytes, dev);
 }
 
-static int finish_out(qxd_ctx* ctx, void* p, const void* dev, size_t bytes, bool host, cudaStream_t st) {
+int finish_out(qxd_ctx* ctx, void* p, const void* dev, size_t bytes, bool host, cudaStream_t st) {
     if (host) {
         QXD_CUDA(ctx, cudaMemcpyAsync(p, dev, bytes, cudaMemcpyDeviceToHost, st));
         QXD_CUDA(ctx, cudaStreamSynchronize(st));
@@ -123,7 +123,7 @@ static int finish_out(qxd_ctx* ctx, void* p, const void* dev, size_t bytes, bool
     return QXD_OK;
 }
 
-static int check_fl(qxd_ctx* ctx, int fl) {
+int check_fl(qxd_ctx* ctx, int fl) {
     if (!ctx) return QXD_EARG;
     if (fl < 0 || fl >= QXD_MAX_FLAVOURS) return qxd_fail(ctx, QXD_EARG, "flavour id out of range 0..7");
     if (!ctx->links_set) return qxd_fail(ctx, QXD_ESTATE, "qxd_set_links has not been called");

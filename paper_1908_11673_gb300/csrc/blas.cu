@@ -329,6 +329,26 @@ int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* 
     return QXD_OK;
 }
 
+// sum of a real FP64 array over its finite entries, and the count of the others
+__global__ void __launch_bounds__(kRedThreads) k_sum_real(size_t n, const double* __restrict__ a, RedOut o) {
+    double v[2] = {0.0, 0.0};
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += S) {
+        const double x = __ldg(a + i);
+        if (isfinite(x)) v[0] += x;
+        else v[1] += 1.0;
+    }
+    block_reduce_finish<2>(v, o);
+}
+
+int blas_sum_real(qxd_ctx* ctx, const double* a, size_t n, int slot, cudaStream_t st) {
+    ProfScope prof(ctx, "sum_real", (double)n * 8, st);
+    const RedOut o = red_out(ctx, slot);
+    k_sum_real<<<wave_blocks(ctx, k_sum_real, kRedThreads, (size_t)kRedThreads, n), kRedThreads, 0, st>>>(n, a, o);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
 int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st) {
     const size_t nc = nchunks(p, n);
     ProfScope prof(ctx, "norm2", (double)n * eb(p), st);

@@ -38,6 +38,9 @@ int sap_check(qxd_ctx* ctx);
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,
                  cudaStream_t st);
+// out = (Dhat^+ Dhat + sigma) v in precision P; tmp_e, tmp_o: even and odd scratch
+int op_normal(qxd_ctx* ctx, int fl, int P, double sigma, const void* v, void* out, void* tmp_e, void* tmp_o,
+              cudaStream_t st);
 // multi-shift CG: b64 even FP64 field, X64 ns consecutive FP64 even fields (output)
 int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solver* s, const void* b64, char* X64,
                qxd_info* info, cudaStream_t st);

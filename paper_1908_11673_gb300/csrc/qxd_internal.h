@@ -99,13 +99,24 @@ int qxd_fail(qxd_ctx* ctx, int code, const std::string& msg);
 // workspace slot `slot` with at least `bytes` bytes (device memory)
 int qxd_ws(qxd_ctx* ctx, int slot, size_t bytes, void** out);
 
+// caller arrays at the C ABI (api.cu): a device view of an input (the array
+// itself when it is device memory, else a copy staged in workspace `slot`); a
+// device destination for an output and whether it must be copied back to the
+// host afterwards (finish_out, which then synchronises); flavour-state checks
+int stage_in(qxd_ctx* ctx, int slot, const void* p, size_t bytes, const void** dev, cudaStream_t st);
+int stage_out(qxd_ctx* ctx, int slot, void* p, size_t bytes, void** dev, bool* host);
+int finish_out(qxd_ctx* ctx, void* p, const void* dev, size_t bytes, bool host, cudaStream_t st);
+int check_fl(qxd_ctx* ctx, int fl);
+
 // workspace slots
 enum {
     WS_STAGE_IN = 0, WS_STAGE_OUT, WS_STAGE_U, WS_STAGE_A,
     WS_T0, WS_T1, WS_T2, WS_T3, WS_T4, WS_T5, WS_T6, WS_T7, WS_T8, WS_T9,
     WS_SOLVER = 32,   // solver vectors start here (up to 128 slots)
     WS_PTC = 192,
-    WS_NSLOTS = 256
+    WS_SAP = 272,
+    WS_RAT = 288,
+    WS_NSLOTS = 320
 };
 
 // kernels launched from other translation units ------------------------------------

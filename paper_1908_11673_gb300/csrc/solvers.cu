@@ -417,7 +417,7 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
 namespace qxd {
 
 // out = (Dhat^+ Dhat + sigma) v in precision P (tmp_e, tmp_o scratch)
-static int op_normal(qxd_ctx* ctx, int fl, int P, double sigma, const void* v, void* out, void* tmp_e, void* tmp_o,
+int op_normal(qxd_ctx* ctx, int fl, int P, double sigma, const void* v, void* out, void* tmp_e, void* tmp_o,
                      cudaStream_t st) {
     const size_t n = 12ull * ctx->g.Vh;
     QXD_TRY(op_Dhat(ctx, fl, P, 0, v, tmp_e, tmp_o, st));

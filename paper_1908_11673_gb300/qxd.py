@@ -26,6 +26,7 @@ STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: 
 EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_apply_Dw",
            "qxd_apply_Dhat_eo", "qxd_apply_Dhat_eo_noalloc", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
            "qxd_set_sap", "qxd_sap_apply", "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
+           "qxd_rat_apply", "qxd_pf_action", "qxd_rw_rat", "qxd_rw_rtm", "qxd_sdet",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -47,6 +48,23 @@ class Flavour(ctypes.Structure):
 class Solver(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("tol", ctypes.c_double), ("nmx", ctypes.c_int), ("nkv", ctypes.c_int),
                 ("inner", ctypes.c_int), ("inner_tol", ctypes.c_double), ("precond", ctypes.c_int)]
+
+
+class Rational(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("A", ctypes.c_double), ("nu", ctypes.POINTER(ctypes.c_double)),
+                ("mu", ctypes.POINTER(ctypes.c_double))]
+
+
+def rational(A, nu, mu):
+    """qxd_rational for coefficients (A, nu[], mu[]); keeps the arrays alive on the result."""
+    nu = np.ascontiguousarray(nu, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    if nu.shape != mu.shape or nu.ndim != 1:
+        raise ValueError("nu and mu must be 1-D arrays of the same length")
+    r = Rational(len(nu), float(A), nu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    r._keep = (nu, mu)
+    return r
 
 
 class Info(ctypes.Structure):
@@ -86,6 +104,15 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(d), vp, vp]),
         "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, ctypes.POINTER(i), vp, vp]),
         "qxd_ptc_record_pairs": (i, [vp, i, vp, i, i, vp, vp, vp]),
+        "qxd_rat_apply": (i, [vp, i, ctypes.POINTER(Rational), i, i, ctypes.POINTER(Solver), vp, vp,
+                              ctypes.POINTER(Info), vp]),
+        "qxd_pf_action": (i, [vp, i, ctypes.POINTER(Rational), i, i, ctypes.POINTER(Solver), vp,
+                              ctypes.POINTER(d), ctypes.POINTER(Info), vp]),
+        "qxd_rw_rat": (i, [vp, i, ctypes.POINTER(Rational), i, i, i, ctypes.POINTER(Solver), vp, vp,
+                           ctypes.POINTER(d), ctypes.POINTER(Info), vp]),
+        "qxd_rw_rtm": (i, [vp, i, ctypes.POINTER(Rational), ctypes.POINTER(Rational), i, i,
+                           ctypes.POINTER(Solver), vp, ctypes.POINTER(d), ctypes.POINTER(Info), vp]),
+        "qxd_sdet": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), vp]),
         "qxd_profile": (i, [vp, i]),
         "qxd_profile_entry": (i, [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -204,6 +231,55 @@ class Context:
         if check:
             self._check(rc)
         return info
+
+    # ---- rational factors, reweighting, small determinant (App. A.2, A.3) -------
+    def _msolver(self, tol, nmx, inner):
+        return Solver(MSCG, float(tol), int(nmx), 0, int(inner), 0.0, PRECOND_NONE)
+
+    def rat_apply(self, fl, r, k, l, in_e, out_e, tol=1e-10, nmx=20000, inner=FP32, stream=None):
+        """out_e = P_{k,l} in_e (r: a qxd.Rational from qxd.rational)."""
+        info = Info()
+        s = self._msolver(tol, nmx, inner)
+        self._check(self.lib.qxd_rat_apply(self._h, int(fl), ctypes.byref(r), int(k), int(l), ctypes.byref(s),
+                                           _ptr(in_e), _ptr(out_e), ctypes.byref(info), _stream(stream)))
+        return info
+
+    def pf_action(self, fl, r, k, l, phi_e, tol=1e-10, nmx=20000, inner=FP32, stream=None):
+        """(phi, P_{k,l} phi); returns (S, info)."""
+        info = Info()
+        S = ctypes.c_double()
+        s = self._msolver(tol, nmx, inner)
+        self._check(self.lib.qxd_pf_action(self._h, int(fl), ctypes.byref(r), int(k), int(l), ctypes.byref(s),
+                                           _ptr(phi_e), ctypes.byref(S), ctypes.byref(info), _stream(stream)))
+        return S.value, info
+
+    def rw_rat(self, fl, r, u, v, nterms, eta_e, tol=1e-10, nmx=20000, inner=FP32, stream=None):
+        """((eta, Z^n eta) for n = 1..nterms, exponent, info)."""
+        info = Info()
+        terms = np.zeros(int(nterms), dtype=np.float64)
+        e = ctypes.c_double()
+        s = self._msolver(tol, nmx, inner)
+        self._check(self.lib.qxd_rw_rat(self._h, int(fl), ctypes.byref(r), int(u), int(v), int(nterms),
+                                        ctypes.byref(s), _ptr(eta_e), terms.ctypes.data, ctypes.byref(e),
+                                        ctypes.byref(info), _stream(stream)))
+        return terms, e.value, info
+
+    def rw_rtm(self, fl, r_mu, r_t, k, l, eta_e, tol=1e-10, nmx=20000, inner=FP32, stream=None):
+        """((eta, [Ptilde_{k,l} - 1] eta), info)."""
+        info = Info()
+        e = ctypes.c_double()
+        s = self._msolver(tol, nmx, inner)
+        self._check(self.lib.qxd_rw_rtm(self._h, int(fl), ctypes.byref(r_mu), ctypes.byref(r_t), int(k), int(l),
+                                        ctypes.byref(s), _ptr(eta_e), ctypes.byref(e), ctypes.byref(info),
+                                        _stream(stream)))
+        return e.value, info
+
+    def sdet(self, fl, stream=None):
+        """(sum over odd sites of log|det D_oo(x)|, number of negative determinants)."""
+        ld = ctypes.c_double()
+        nn = ctypes.c_int()
+        self._check(self.lib.qxd_sdet(self._h, int(fl), ctypes.byref(ld), ctypes.byref(nn), _stream(stream)))
+        return ld.value, nn.value
 
     # ---- SAP preconditioner ----------------------------------------------------
     def set_sap(self, ncy=5, nmr=5):
