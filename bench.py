@@ -332,11 +332,12 @@ def run_native(args, w, name):
                                                                                       "nkv": 16})), 1)
             ps = {p["name"]: p for p in ctx.profile_entries()}
             ctx.profile(0)
-            blk = ps.get("sap_block")
+            blk = ps.get("sap_sweep")
             nxt[f"sap_fgcr_ncy{ncy}_nmr{nmr}"] = {
                 "ms": ms_sap, "iters": inf_sap[0].iters, "true_relres": inf_sap[0].true_relres,
-                "sap_block_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
-                "sap_block_launches": blk["launches"] if blk else None}
+                "sap_sweep_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
+                "sap_sweep_launches": blk["launches"] if blk else None,
+                "sap_sweep_GBps": blk["bytes"] / (blk["ms"] * 1e-3) / 1e9 if blk else None}
         A_r, nu_r, mu_r = read_rational(GOLDEN_RATIONAL)
         rat = qxd.rational(A_r, nu_r, mu_r)
         phi_e = torch.from_numpy(np.ascontiguousarray(eta[: V // 2])).to(dev)

@@ -101,7 +101,7 @@ typedef struct {
  *          (0 selects 1e-5 for FP32 and 5e-3 for BF16 storage).
  * precond: right preconditioner of FGCR: QXD_PRECOND_NONE, QXD_PRECOND_LEARNED (the network of
  *          qxd_set_precond_weights) or QXD_PRECOND_SAP (Schwarz alternating procedure, see
- *          qxd_set_sap; needs every simulated extent to be a multiple of 4 and at least 8). */
+ *          qxd_set_sap; needs every simulated extent to be a multiple of 8). */
 typedef struct {
     int kind;
     double tol;
@@ -276,16 +276,16 @@ int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, i
  * Blocks of 4^4 sites coloured like a checkerboard; one application M eta runs
  * ncy cycles over the two colours, each block solving its Dirichlet block system
  * (hops leaving the block dropped) approximately by nmr minimal-residual steps on
- * the block's even-odd system, with the full residual rho = eta - D psi refreshed
- * after every colour.  FGCR on Dhat uses z_e = (M (r_e, 0))_e (Dhat^-1 = (D^-1)_ee).
+ * the block's even-odd system, for the residual rho = eta - D psi taken on the
+ * block at the start of its colour's sweep.  FGCR on Dhat uses z_e = (M (r_e, 0))_e (Dhat^-1 = (D^-1)_ee).
  * Arithmetic in FP32. */
 
 /* Set ncy and nmr (1..64 each; default 5 and 5, the paper's values). */
 int qxd_set_sap(qxd_ctx* ctx, int ncy, int nmr);
 
 /* out = M in on the full lattice, complex64 [V][4][3] (host or device arrays).
- * QXD_EARG unless every simulated extent is a multiple of 4 and at least 8 (two blocks,
- * so that every block face is a Dirichlet boundary).  Synchronises `stream`. */
+ * QXD_EARG unless every simulated extent is a multiple of 8 (an even number of blocks,
+ * so that blocks of one colour never touch).  Synchronises `stream`. */
 int qxd_sap_apply(qxd_ctx* ctx, int fl, const void* in, void* out, void* stream);
 
 /* ---- learned preconditioner: inference and training (not part of the paper) ----

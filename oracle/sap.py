@@ -3,9 +3,10 @@ with block size 4^4, ncy = 5 cycles, nmr = 5 minimal-residual steps).  Plain
 FP64 NumPy.
 
 The lattice is tiled by non-overlapping blocks of b^4 sites, coloured like a
-checkerboard by the parity of the block coordinates.  Every extent must hold at
-least two blocks, so that no hop joins a block to itself across the periodic
-boundary and every block face is a Dirichlet boundary.  The block operator D_B
+checkerboard by the parity of the block coordinates.  Every extent must hold an
+even number of blocks: then blocks of one colour never touch (across the
+periodic boundary included), no hop joins a block to itself, and every block
+face is a Dirichlet boundary.  The block operator D_B
 is D restricted to a block with Dirichlet boundary conditions: hops that leave
 the block are dropped.  One application of the preconditioner M to a source eta:
 
@@ -36,8 +37,8 @@ from .dirac import DiracOperator, GAMMA, ONE4
 class SAP:
     def __init__(self, op: DiracOperator, bsize: int = 4, ncy: int = 5, nmr: int = 5):
         geom = op.geom
-        if any(n % bsize for n in geom.N) or any(n < 2 * bsize for n in geom.N):
-            raise ValueError("every simulated extent must be a multiple of the block size and hold two blocks")
+        if any(n % (2 * bsize) for n in geom.N):
+            raise ValueError("every simulated extent must hold an even number of blocks")
         self.op, self.geom = op, geom
         self.b, self.ncy, self.nmr = bsize, ncy, nmr
         s = geom.sites()

@@ -6,13 +6,20 @@
 // D with Dirichlet block boundaries (hops leaving the block dropped).  One
 // application M eta: psi = 0, rho = eta; ncy times, for each colour: every block
 // of that colour solves its block system approximately (even-odd system of the
-// block, nmr minimal-residual steps from zero), psi += d on the block, and then
-// rho = eta - D psi.  As a preconditioner of Dhat: z_e = (M (r_e, 0))_e.
+// block, nmr minimal-residual steps from zero) for the current residual
+// rho = eta - D psi restricted to the block, and psi += d on the block.  As a
+// preconditioner of Dhat: z_e = (M (r_e, 0))_e.  Every extent must hold an even
+// number of blocks, so that blocks of one colour never touch, across the
+// periodic boundary included.
 //
-// GPU layout: one CTA per block, 128 threads; thread t owns the t-th even and the
-// t-th odd site of the block.  The block's residual and odd intermediate live in
-// shared memory; links and site-diagonal terms are read from global memory (the
-// nmr steps re-read them from L1/L2).  FP32 throughout, block sums in FP32.
+// GPU layout: one launch per colour sweep, one CTA per block, 128 threads; thread
+// t owns the t-th even and the t-th odd site of the block.  The block's links are
+// staged in shared memory once per sweep, so the 2 nmr + 2 block hops of the
+// minimal-residual steps read links and neighbour spinors from shared memory only.
+// The sweep also computes the block residual rho = eta - D psi itself (the
+// other colour's psi on the one-site halo comes from global memory), so no
+// full-lattice residual is formed between colours.  Site-diagonal terms are
+// streamed from global memory.  FP32 throughout, block sums in FP32.
 #include <cmath>
 
 #include "blas.h"
@@ -22,16 +29,17 @@
 
 namespace qxd {
 
-constexpr int kSapB = 4;       // block extent
+constexpr int kSapB = 4;          // block extent
 constexpr int kSapThreads = 128;  // half of the 4^4 block sites
+constexpr int kSapSites = 256;
 
 struct SapDev {
     int nb[4];              // blocks per direction
     const float4* U32[2];   // links per parity
     const float4* Z32[2];   // phases per parity
-    const float4* Aee;      // diagonal term, even sites
-    const float4* Aoo_inv;  // inverse diagonal term, odd sites
-    const float4* rho;      // residual, full field (even half, odd half)
+    const float4* A[2];     // site-diagonal term per parity
+    const float4* Aoo_inv;  // its inverse, odd sites
+    const float4* eta;      // source, full field (even half, odd half)
     float4* psi;            // solution, full field
     int nmr;
 };
@@ -42,9 +50,17 @@ struct SiteRef {
     int h;     // half index of the site
 };
 
+// shared memory of one block: its links, two half-block spinor buffers and the
+// odd residual, all structure-of-arrays over the block's sites
+struct SapShared {
+    float2 lk[4][7][kSapSites];      // U rows 0, 1 (6 complex) and z^qhat, per direction and local site
+    float2 sp[2][12][kSapThreads];   // spinor buffers by parity
+    float2 rho_o[12][kSapThreads];   // residual on the odd sites
+    float red[3 * kSapThreads / 32];
+};
+
 // the t-th site of parity p in block bc
 __device__ __forceinline__ void block_site(const Geo& g, const int bc[4], int p, int t, SiteRef& s) {
-    s.l[3] = 0;
     int r = t;
     const int x3h = r & 1;
     r >>= 1;
@@ -57,82 +73,128 @@ __device__ __forceinline__ void block_site(const Geo& g, const int bc[4], int p,
     s.h = lex_index(g, s.x) >> 1;
 }
 
-// thread index of the local site l (any parity)
+// thread index of the local site l within its parity
 __device__ __forceinline__ int block_thread(const int l[4]) { return (((l[0] * 4 + l[1]) * 4 + l[2]) * 2) + (l[3] >> 1); }
 
-__device__ __forceinline__ void load_sm(const float2* __restrict__ sm, int t, cplx<float> s[12]) {
+__device__ __forceinline__ void load_sm(const float2 (*sm)[kSapThreads], int t, cplx<float> s[12]) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        float2 v = sm[t * 12 + k];
+        const float2 v = sm[k][t];
         s[k] = {v.x, v.y};
     }
 }
-__device__ __forceinline__ void store_sm(float2* __restrict__ sm, int t, const cplx<float> s[12]) {
+__device__ __forceinline__ void store_sm(float2 (*sm)[kSapThreads], int t, const cplx<float> s[12]) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sm[t * 12 + k] = make_float2(s[k].re, s[k].im);
+    for (int k = 0; k < 12; ++k) sm[k][t] = make_float2(s[k].re, s[k].im);
 }
 
-// acc += hopping term at site s (parity p) from the opposite-parity field in
-// shared memory, hops leaving the block dropped.  acc = -1/2 sum_mu [...].
-template <int MU>
-__device__ __forceinline__ void hop_dir_block(const Geo& g, const SapDev& a, const SiteRef& s, int p,
-                                              const float2* __restrict__ sm, cplx<float> acc[12]) {
-    const int Vh = g.Vh;
+// link of direction mu at the block's local site sid (= parity * 128 + thread) from shared memory
+__device__ __forceinline__ void link_sm(const SapShared& S, int mu, int sid, Mat3<float>& m, cplx<float>& z) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float2 v = S.lk[mu][3 * i + j][sid];
+            m.a[i][j] = {v.x, v.y};
+        }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        m.a[2][j] = conj(m.a[0][j1] * m.a[1][j2] - m.a[0][j2] * m.a[1][j1]);
+    }
+    const float2 zz = S.lk[mu][6][sid];
+    z = {zz.x, zz.y};
+}
+
+__device__ __forceinline__ void phase_mul(cplx<float> z, bool dag, Half<float>& o) {
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o.a[sp][c] = dag ? cmul_conj(z, o.a[sp][c]) : z * o.a[sp][c];
+}
+
+// acc += hop terms of direction MU at site s (parity p) from the opposite-parity
+// spinor buffer nb.  HALO = false: hops leaving the block are dropped (block
+// operator).  HALO = true: they take the spinor of the neighbouring site from the
+// global field nb_glob (opposite parity) and, backwards, its link from global memory.
+template <int MU, bool HALO>
+__device__ __forceinline__ void hop_dir_sap(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
+                                            const float2 (*nb)[kSapThreads], const float4* nb_glob,
+                                            cplx<float> acc[12]) {
     Half<float> hp, o;
     Mat3<float> m;
     cplx<float> z;
     cplx<float> v[12];
-    if (s.l[MU] + 1 < kSapB) {
-        int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
-        ln[MU] += 1;
-        load_sm(sm, block_thread(ln), v);
+    const int sid = p * kSapThreads + block_thread(s.l);
+    if (s.l[MU] + 1 < kSapB || HALO) {
+        if (s.l[MU] + 1 < kSapB) {
+            int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
+            ln[MU] += 1;
+            load_sm(nb, block_thread(ln), v);
+        } else {
+            load_spinor<1>(nb_glob, g.Vh, neighbour_lex(g, s.x, MU, +1) >> 1, v);
+        }
         project<MU, true>(v, hp);
-        load_link32(a.U32[p], a.Z32[p], Vh, MU, s.h, m, z);
+        link_sm(S, MU, sid, m, z);
         mul_half<false>(m, hp, o);
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o.a[sp][c] = z * o.a[sp][c];
+        phase_mul(z, false, o);
         reconstruct<MU, true>(o, acc);
     }
-    if (s.l[MU] > 0) {
-        int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
-        ln[MU] -= 1;
-        load_sm(sm, block_thread(ln), v);
+    if (s.l[MU] > 0 || HALO) {
+        if (s.l[MU] > 0) {
+            int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
+            ln[MU] -= 1;
+            const int tn = block_thread(ln);
+            load_sm(nb, tn, v);
+            link_sm(S, MU, (1 - p) * kSapThreads + tn, m, z);
+        } else {
+            const int hn = neighbour_lex(g, s.x, MU, -1) >> 1;
+            load_spinor<1>(nb_glob, g.Vh, hn, v);
+            load_link32(a.U32[1 - p], a.Z32[1 - p], g.Vh, MU, hn, m, z);
+        }
         project<MU, false>(v, hp);
-        int xn[4] = {s.x[0], s.x[1], s.x[2], s.x[3]};
-        xn[MU] -= 1;
-        const int hn = lex_index(g, xn) >> 1;
-        load_link32(a.U32[1 - p], a.Z32[1 - p], Vh, MU, hn, m, z);
         mul_half<true>(m, hp, o);
-#pragma unroll
-        for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o.a[sp][c] = cmul_conj(z, o.a[sp][c]);
+        phase_mul(z, true, o);
         reconstruct<MU, false>(o, acc);
     }
 }
 
-// out = -1/2 sum_mu [...] (block hopping term) at site s of parity p
-__device__ __forceinline__ void hop_block(const Geo& g, const SapDev& a, const SiteRef& s, int p,
-                                          const float2* __restrict__ sm, cplx<float> out[12]) {
+// out = -1/2 sum_mu [...] at site s of parity p (block operator, or with the halo)
+template <bool HALO>
+__device__ __forceinline__ void hop_sap(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
+                                        const float2 (*nb)[kSapThreads], const float4* nb_glob, cplx<float> out[12]) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = {0.f, 0.f};
-    hop_dir_block<0>(g, a, s, p, sm, out);
-    hop_dir_block<1>(g, a, s, p, sm, out);
-    hop_dir_block<2>(g, a, s, p, sm, out);
-    hop_dir_block<3>(g, a, s, p, sm, out);
+    hop_dir_sap<0, HALO>(g, a, S, s, p, nb, nb_glob, out);
+    hop_dir_sap<1, HALO>(g, a, S, s, p, nb, nb_glob, out);
+    hop_dir_sap<2, HALO>(g, a, S, s, p, nb, nb_glob, out);
+    hop_dir_sap<3, HALO>(g, a, S, s, p, nb, nb_glob, out);
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = -0.5f * out[k];
 }
 
+// s = D s for a packed site-diagonal term (two Hermitian 6x6 blocks), streamed
+// from global memory one block at a time
 __device__ __forceinline__ void diag_mul(const float4* __restrict__ D, int Vh, int h, cplx<float> s[12]) {
-    float d[72];
-    load_diag<1>(D, Vh, h, d);
-    apply_diag(d, s);
+#pragma unroll
+    for (int blk = 0; blk < 2; ++blk) {
+        float d[36];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float4 v = QXD_LDG(D + (size_t)(blk * 9 + k) * Vh + h);
+            d[4 * k] = v.x;
+            d[4 * k + 1] = v.y;
+            d[4 * k + 2] = v.z;
+            d[4 * k + 3] = v.w;
+        }
+        cplx<float> o[6];
+        herm6_mul(d, s + 6 * blk, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s[6 * blk + i] = o[i];
+    }
 }
 
-// sum over the CTA of two complex numbers (re, im of <p, r>) and a real (|p|^2)
+// sum over the CTA of three floats
 __device__ __forceinline__ void cta_sum3(float v[3], float* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -150,10 +212,16 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* sh) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kSapThreads) k_sap_block(Geo g, SapDev a, int colour) {
-    __shared__ float2 sm_e[kSapThreads * 12];  // block residual / solution on even sites
-    __shared__ float2 sm_o[kSapThreads * 12];  // odd intermediate
-    __shared__ float red[3 * kSapThreads / 32];
+// One colour sweep of SAP: every block of colour `colour` (one CTA each) takes
+// its residual rho = eta - D psi (FIRST: psi = 0, so rho = eta), solves its
+// Dirichlet block system approximately by nmr minimal-residual steps on the
+// block's even-odd system, and adds the block solution to psi.  Blocks of one
+// colour never touch, so every CTA reads the other colour's psi on its halo
+// and writes its own sites only.
+template <bool FIRST>
+__global__ void __launch_bounds__(kSapThreads) k_sap_sweep(Geo g, SapDev a, int colour) {
+    extern __shared__ __align__(16) unsigned char sap_smem[];
+    SapShared& S = *reinterpret_cast<SapShared*>(sap_smem);
     int bc[4];
     {
         int b = blockIdx.x;
@@ -170,33 +238,82 @@ __global__ void __launch_bounds__(kSapThreads) k_sap_block(Geo g, SapDev a, int 
     SiteRef se, so;
     block_site(g, bc, 0, t, se);
     block_site(g, bc, 1, t, so);
-    cplx<float> rho_e[12], v[12], r[12], y[12], p[12];
-    load_spinor<1>(a.rho, Vh, se.h, rho_e);
-    // t_o = A_oo^-1 rho_o
-    load_spinor<1>(a.rho + 6 * (size_t)Vh, Vh, so.h, v);
-    diag_mul(a.Aoo_inv, Vh, so.h, v);
-    store_sm(sm_o, t, v);
+    // the block's links into shared memory (this thread: its even and its odd site)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int h = p == 0 ? se.h : so.h;
+        const int sid = p * kSapThreads + t;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            const float4 c0 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 0) * Vh + h);
+            const float4 c1 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 1) * Vh + h);
+            const float4 c2 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 2) * Vh + h);
+            S.lk[mu][0][sid] = make_float2(c0.x, c0.y);
+            S.lk[mu][1][sid] = make_float2(c0.z, c0.w);
+            S.lk[mu][2][sid] = make_float2(c1.x, c1.y);
+            S.lk[mu][3][sid] = make_float2(c1.z, c1.w);
+            S.lk[mu][4][sid] = make_float2(c2.x, c2.y);
+            S.lk[mu][5][sid] = make_float2(c2.z, c2.w);
+        }
+        const float4 z01 = QXD_LDG(a.Z32[p] + h);
+        const float4 z23 = QXD_LDG(a.Z32[p] + (size_t)Vh + h);
+        S.lk[0][6][sid] = make_float2(z01.x, z01.y);
+        S.lk[1][6][sid] = make_float2(z01.z, z01.w);
+        S.lk[2][6][sid] = make_float2(z23.x, z23.y);
+        S.lk[3][6][sid] = make_float2(z23.z, z23.w);
+    }
+    const float4* psi_e = a.psi;
+    const float4* psi_o = a.psi + 6 * (size_t)Vh;
+    cplx<float> v[12], r[12], y[12], p[12];
+    // residual rho = eta - D psi on the block's sites: r (even), rho_o (odd, shared)
+    load_spinor<1>(a.eta, Vh, se.h, r);
+    load_spinor<1>(a.eta + 6 * (size_t)Vh, Vh, so.h, y);
+    if (!FIRST) {
+        load_spinor<1>(psi_e, Vh, se.h, v);
+        store_sm(S.sp[0], t, v);
+        load_spinor<1>(psi_o, Vh, so.h, p);
+        store_sm(S.sp[1], t, p);
+        __syncthreads();
+        // even site: A_ee psi_e + H_eo psi_o
+        diag_mul(a.A[0], Vh, se.h, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = r[k] - v[k];
+        hop_sap<true>(g, a, S, se, 0, S.sp[1], psi_o, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) r[k] = r[k] - v[k];
+        // odd site: A_oo psi_o + H_oe psi_e
+        diag_mul(a.A[1], Vh, so.h, p);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = y[k] - p[k];
+        hop_sap<true>(g, a, S, so, 1, S.sp[0], psi_e, v);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) y[k] = y[k] - v[k];
+    }
+    store_sm(S.rho_o, t, y);
+    // t_o = A_oo^-1 rho_o;  b_e = rho_e - H^B_eo t_o
+    diag_mul(a.Aoo_inv, Vh, so.h, y);
+    __syncthreads();  // every thread is done with the psi buffers
+    store_sm(S.sp[1], t, y);
     __syncthreads();
-    // b_e = rho_e - H^B_eo t_o
-    hop_block(g, a, se, 0, sm_o, v);
+    hop_sap<false>(g, a, S, se, 0, S.sp[1], nullptr, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-        r[k] = rho_e[k] - v[k];
+        r[k] = r[k] - v[k];
         y[k] = {0.f, 0.f};
     }
-    store_sm(sm_e, t, r);
+    store_sm(S.sp[0], t, r);
     __syncthreads();
     for (int it = 0; it < a.nmr; ++it) {
         // t_o = A_oo^-1 H^B_oe r_e
-        hop_block(g, a, so, 1, sm_e, v);
+        hop_sap<false>(g, a, S, so, 1, S.sp[0], nullptr, v);
         diag_mul(a.Aoo_inv, Vh, so.h, v);
-        store_sm(sm_o, t, v);
+        store_sm(S.sp[1], t, v);
         __syncthreads();
-        // p = A_ee r - H^B_eo t_o
-        hop_block(g, a, se, 0, sm_o, v);
+        // p = Dhat_B r = A_ee r - H^B_eo t_o
+        hop_sap<false>(g, a, S, se, 0, S.sp[1], nullptr, v);
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[k] = r[k];
-        diag_mul(a.Aee, Vh, se.h, p);
+        diag_mul(a.A[0], Vh, se.h, p);
         float s3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -205,52 +322,48 @@ __global__ void __launch_bounds__(kSapThreads) k_sap_block(Geo g, SapDev a, int 
             s3[1] += p[k].re * r[k].im - p[k].im * r[k].re;
             s3[2] += p[k].re * p[k].re + p[k].im * p[k].im;
         }
-        cta_sum3(s3, red);
+        cta_sum3(s3, S.red);
         const cplx<float> alpha = s3[2] > 0.f ? cplx<float>{s3[0] / s3[2], s3[1] / s3[2]} : cplx<float>{0.f, 0.f};
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             cmac(y[k], alpha, r[k]);
             r[k] = r[k] - alpha * p[k];
         }
-        store_sm(sm_e, t, r);
+        store_sm(S.sp[0], t, r);
         __syncthreads();
     }
     // d_o = A_oo^-1 (rho_o - H^B_oe y);  psi += d
-    store_sm(sm_e, t, y);
+    store_sm(S.sp[0], t, y);
     __syncthreads();
-    hop_block(g, a, so, 1, sm_e, v);
-    cplx<float> rho_o[12];
-    load_spinor<1>(a.rho + 6 * (size_t)Vh, Vh, so.h, rho_o);
+    hop_sap<false>(g, a, S, so, 1, S.sp[0], nullptr, v);
+    load_sm(S.rho_o, t, p);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = rho_o[k] - v[k];
+    for (int k = 0; k < 12; ++k) v[k] = p[k] - v[k];
     diag_mul(a.Aoo_inv, Vh, so.h, v);
-    cplx<float> ps[12];
-    load_spinor<1>(a.psi, Vh, se.h, ps);
+    if (!FIRST) {
+        load_spinor<1>(psi_e, Vh, se.h, p);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k] = ps[k] + y[k];
-    store_spinor<1>(a.psi, Vh, se.h, ps);
-    load_spinor<1>(a.psi + 6 * (size_t)Vh, Vh, so.h, ps);
+        for (int k = 0; k < 12; ++k) y[k] = y[k] + p[k];
+        load_spinor<1>(psi_o, Vh, so.h, p);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k] = ps[k] + v[k];
-    store_spinor<1>(a.psi + 6 * (size_t)Vh, Vh, so.h, ps);
+        for (int k = 0; k < 12; ++k) v[k] = v[k] + p[k];
+    }
+    store_spinor<1>(a.psi, Vh, se.h, y);
+    store_spinor<1>(a.psi + 6 * (size_t)Vh, Vh, so.h, v);
 }
 
 int sap_check(qxd_ctx* ctx) {
     for (int mu = 0; mu < 4; ++mu)
-        if (ctx->g.N[mu] % kSapB || ctx->g.N[mu] < 2 * kSapB)
-            return qxd_fail(ctx, QXD_EARG, "SAP: every simulated extent must be a multiple of 4 and at least 8");
+        if (ctx->g.N[mu] % (2 * kSapB))
+            return qxd_fail(ctx, QXD_EARG, "SAP: every simulated extent must be a multiple of 8 (an even number of 4^4 blocks)");
     return QXD_OK;
 }
 
-// psi = M eta on full FP32 fields (even half then odd half)
+// psi = M eta on full FP32 fields (even half then odd half); psi must not alias eta
 int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStream_t st) {
     QXD_TRY(sap_check(ctx));
     const Geo& g = ctx->g;
     const size_t hb = half_bytes(ctx, QXD_FP32);
-    const size_t n2 = 24ull * g.Vh;  // complex numbers of a full field
-    void *rho, *dpsi;
-    QXD_TRY(qxd_ws(ctx, WS_SAP + 0, 2 * hb, &rho));
-    QXD_TRY(qxd_ws(ctx, WS_SAP + 1, 2 * hb, &dpsi));
     const QxdFlavour& F = ctx->fl[fl];
     SapDev a;
     int nblk = 1;
@@ -261,29 +374,27 @@ int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStr
     for (int p = 0; p < 2; ++p) {
         a.U32[p] = ctx->U32 + (size_t)p * 12 * g.Vh;
         a.Z32[p] = F.Z32 + (size_t)p * 2 * g.Vh;
+        a.A[p] = F.C32[0] + (size_t)p * 18 * g.Vh;
     }
-    a.Aee = F.C32[0];
     a.Aoo_inv = F.C32[1] + (size_t)18 * g.Vh;
-    a.rho = static_cast<const float4*>(rho);
+    a.eta = eta;
     a.psi = psi;
     a.nmr = ctx->sap_nmr;
+    const int smem = (int)sizeof(SapShared);
+    QXD_CUDA(ctx, cudaFuncSetAttribute(k_sap_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    QXD_CUDA(ctx, cudaFuncSetAttribute(k_sap_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     QXD_CUDA(ctx, cudaMemsetAsync(psi, 0, 2 * hb, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(rho, eta, 2 * hb, cudaMemcpyDeviceToDevice, st));
-    char* pc = reinterpret_cast<char*>(psi);
-    char* rc = static_cast<char*>(rho);
-    char* dc = static_cast<char*>(dpsi);
+    // algorithmic bytes per site of a sweep's colour: own links 224, eta 96, psi of the
+    // block and its halo 192, psi written 96, A 288, A_oo^-1 on odd sites 144, halo links 56
+    const double site_bytes = 224 + 96 + 192 + 96 + 288 + 144 + 56;
     for (int cy = 0; cy < ctx->sap_ncy; ++cy) {
         for (int colour = 0; colour < 2; ++colour) {
-            {
-                ProfScope prof(ctx, "sap_block", (double)g.Vh * 2 * (96 * 3 + 4 * 56 + 288), st);
-                k_sap_block<<<nblk, kSapThreads, 0, st>>>(g, a, colour);
-                QXD_CUDA(ctx, cudaGetLastError());
-            }
-            if (cy == ctx->sap_ncy - 1 && colour == 1) break;
-            // rho = eta - D psi
-            QXD_TRY(op_Dw(ctx, fl, QXD_FP32, Full{pc, pc + hb}, Full{dc, dc + hb}, st));
-            QXD_CUDA(ctx, cudaMemcpyAsync(rc, eta, 2 * hb, cudaMemcpyDeviceToDevice, st));
-            QXD_TRY(blas_axpby(ctx, 1, 1, n2, -1.0, 0.0, dc, 1.0, 0.0, rc, st));
+            ProfScope prof(ctx, "sap_sweep", (double)g.Vh * site_bytes, st);
+            if (cy == 0 && colour == 0)
+                k_sap_sweep<true><<<nblk, kSapThreads, smem, st>>>(g, a, colour);
+            else
+                k_sap_sweep<false><<<nblk, kSapThreads, smem, st>>>(g, a, colour);
+            QXD_CUDA(ctx, cudaGetLastError());
         }
     }
     return QXD_OK;

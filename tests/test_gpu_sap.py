@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("L,cstar,ncy,nmr", [((8, 8, 8, 8), 0, 1, 1), ((8, 8, 8, 8), 0, 5, 5),
-                                              ((12, 8, 8, 8), 0, 1, 2), ((8, 4, 8, 8), 1, 2, 3),
+                                              ((16, 8, 8, 8), 0, 1, 2), ((8, 4, 8, 8), 1, 2, 3),
                                               ((8, 4, 8, 8), 3, 5, 5)])
 def test_sap_apply_parity(L, cstar, ncy, nmr):
     qxd, ctx, op, _, _ = setup(L, cstar, (np.pi, 0, 0, 0), qhat=4, kappa=0.13, seed=9100, stout=1)
@@ -45,9 +45,9 @@ def test_sap_fgcr_solves(inner):
     ctx.close()
 
 
-@pytest.mark.parametrize("L", [(6, 8, 8, 8), (8, 8, 4, 8)])
+@pytest.mark.parametrize("L", [(6, 8, 8, 8), (8, 8, 4, 8), (12, 8, 8, 8)])
 def test_sap_rejects_unsupported_lattices(L):
-    """Extents must be multiples of 4 holding at least two blocks."""
+    """Extents must hold an even number of 4^4 blocks."""
     qxd, ctx, op, _, _ = setup(L, 0, (np.pi, 0, 0, 0))
     eta = workload.spinor(op.geom.V, 1).astype(np.complex64)
     with pytest.raises(qxd.QxdError) as e:

@@ -49,11 +49,12 @@ def test_sap_iteration_converges_to_the_solution():
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3, errs
 
 
-@pytest.mark.parametrize("L", [(2, 4, 4, 4), (4, 4, 6, 4)])
-def test_sap_needs_two_blocks_per_direction(L):
+@pytest.mark.parametrize("L,b", [((2, 4, 4, 4), 2), ((4, 4, 6, 4), 2), ((4, 4, 6, 4), 4)])
+def test_sap_needs_an_even_number_of_blocks(L, b):
+    """one block, three blocks, and an extent that is no multiple of the block size"""
     op, _, _ = make_op(L, 0, (np.pi, 0, 0, 0))
     with pytest.raises(ValueError):
-        SAP(op, bsize=2 if L[2] == 4 else 4)
+        SAP(op, bsize=b)
 
 
 def test_sap_is_gauge_covariant():
