@@ -62,7 +62,7 @@ typedef enum { QXD_FP64 = 0, QXD_FP32 = 1, QXD_BF16 = 2 } qxd_prec;
 
 typedef enum { QXD_CGNE = 0, QXD_FGCR = 1, QXD_MSCG = 2 } qxd_solver_kind;
 
-typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1, QXD_PRECOND_SAP = 2 } qxd_precond_kind;
+typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1, QXD_PRECOND_SAP = 2, QXD_PRECOND_DFL = 3 } qxd_precond_kind;
 
 /* Geometry (Sec. 2.1).  Every L[mu] must be even and >= 2.
  * cstar in 0..3: C* boundary conditions in directions 1..cstar.
@@ -101,7 +101,8 @@ typedef struct {
  *          (0 selects 1e-5 for FP32 and 5e-3 for BF16 storage).
  * precond: right preconditioner of FGCR: QXD_PRECOND_NONE, QXD_PRECOND_LEARNED (the network of
  *          qxd_set_precond_weights) or QXD_PRECOND_SAP (Schwarz alternating procedure, see
- *          qxd_set_sap; needs every simulated extent to be a multiple of 8). */
+ *          qxd_set_sap; needs every simulated extent to be a multiple of 8) or
+ *          QXD_PRECOND_DFL (inexact deflation with SAP, see qxd_dfl_setup). */
 typedef struct {
     int kind;
     double tol;
@@ -287,6 +288,44 @@ int qxd_set_sap(qxd_ctx* ctx, int ncy, int nmr);
  * QXD_EARG unless every simulated extent is a multiple of 8 (an even number of blocks,
  * so that blocks of one colour never touch).  Synchronises `stream`. */
 int qxd_sap_apply(qxd_ctx* ctx, int fl, const void* in, void* out, void* stream);
+
+/* ---- inexact deflation with SAP (Sec. 4.4: DFL+SAP+GCR) ----
+ * One deflation subspace per flavour slot, hence per charge.  Blocks are the SAP
+ * blocks (4^4; every simulated extent a multiple of 8).  The subspace is built
+ * from Ns given random fields: ninv times phi_k <- M_sap phi_k (SAP with the
+ * context's ncy, nmr), each time followed by Gram-Schmidt of the restrictions
+ * phi_k|_B on every block B.  P c = sum_{B,k} c_{B,k} phi_k|_B, P^+ its adjoint,
+ * A = P^+ D P the little Dirac operator.  The preconditioner is
+ *   M_dfl v = P A^-1 P^+ v + M_sap (v - D P A^-1 P^+ v),
+ * with A^-1 from GCR on the block grid (restart cnkv, at most cnmx steps, relative
+ * residual ctol); FGCR on Dhat uses z_e = (M_dfl (r_e, 0))_e.  FP32 throughout. */
+typedef struct {
+    int Ns;       /* vectors per block, 1..32 */
+    int ninv;     /* inverse-iteration steps with SAP, 0..64 */
+    double ctol;  /* relative residual of the little-system solves */
+    int cnmx;     /* maximum GCR steps of a little-system solve */
+    int cnkv;     /* GCR restart length of the little-system solver, 1..32 */
+} qxd_dfl_params;
+
+/* Build the subspace and A for flavour fl.  seeds: complex64 [Ns][V][4][3] random
+ * start fields (host or device).  Replaces an earlier subspace of fl; dropped when
+ * the links or the SW term of fl change.  QXD_EARG for bad parameters or a lattice
+ * SAP does not support.  Synchronises `stream`. */
+int qxd_dfl_setup(qxd_ctx* ctx, int fl, const qxd_dfl_params* p, const void* seeds, void* stream);
+
+/* Basis field phi_k (block-orthonormal), complex64 [V][4][3] (host or device). */
+int qxd_dfl_basis(qxd_ctx* ctx, int fl, int k, void* out, void* stream);
+
+/* The little operator: A_out (may be NULL) complex64 [Nb][9][Ns][Ns] with
+ * A_out[B][s][l][k] = <phi_k|_B, D phi_l|_{B_s}>; nbr_out (may be NULL) int [Nb][9]
+ * the block B_s of slot s (0: B; 1 + 2 mu: across the +mu face; 2 + 2 mu: across
+ * the -mu face); *nblocks (may be NULL) = Nb.  Blocks are numbered
+ * lexicographically by block coordinates, x0 slowest. */
+int qxd_dfl_little(qxd_ctx* ctx, int fl, void* A_out, int* nbr_out, int* nblocks, void* stream);
+
+/* out = M_dfl in on the full lattice, complex64 [V][4][3] (host or device).
+ * info (may be NULL): iters and true_relres of the little-system GCR. */
+int qxd_dfl_apply(qxd_ctx* ctx, int fl, const void* in, void* out, qxd_info* info, void* stream);
 
 /* ---- learned preconditioner: inference and training (not part of the paper) ----
  * The network M and its weight layout are those of qxd_set_precond_weights.

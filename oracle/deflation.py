@@ -47,6 +47,20 @@ class Deflation:
             self.phis = self.orthonormalise(phis)
         self.A = self.little_operator()
 
+    @classmethod
+    def from_basis(cls, op: DiracOperator, sap: SAP, phis):
+        """The same construction for a given basis (taken as it is, not regenerated
+        or re-orthonormalised): lets a test evaluate A and M_dfl on another
+        implementation's subspace."""
+        self = cls.__new__(cls)
+        self.op, self.sap, self.geom = op, sap, op.geom
+        self.block = sap.block
+        self.nblocks = sap.nblocks
+        self.phis = np.array(phis, dtype=np.complex128)
+        self.Ns = len(self.phis)
+        self.A = self.little_operator()
+        return self
+
     # --- blocks ---------------------------------------------------------------
     def block_dot(self, a, b):
         """<a|_B, b|_B> for every block B (complex, length Nb)."""

@@ -139,6 +139,9 @@ static void free_flavour(QxdFlavour& F) {
         cudaFree(F.C32[k]);
     }
     cudaFree(F.W);
+    cudaFree(F.dfl_basis);
+    cudaFree(F.dfl_A);
+    cudaFree(F.dfl_nbr);
     F = QxdFlavour{};
 }
 
@@ -253,6 +256,14 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
     }
     F.f = *f;
     F.set = false;
+    // a deflation subspace belongs to the operator it was built for
+    cudaFree(F.dfl_basis);
+    cudaFree(F.dfl_A);
+    cudaFree(F.dfl_nbr);
+    F.dfl_basis = nullptr;
+    F.dfl_A = nullptr;
+    F.dfl_nbr = nullptr;
+    F.dfl_Ns = 0;
     QXD_TRY(launch_set_flavour(ctx, fl, st));
     F.set = true;
     return QXD_OK;
@@ -320,8 +331,10 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
         return qxd_fail(ctx, QXD_EARG, "solve: inner precision must be 0, 1 or 2");
     if (s->precond == QXD_PRECOND_LEARNED && !ctx->fl[fl].W)
         return qxd_fail(ctx, QXD_ESTATE, "solve: learned preconditioner weights not set");
-    if (s->precond < 0 || s->precond > QXD_PRECOND_SAP) return qxd_fail(ctx, QXD_EARG, "solve: unknown preconditioner");
+    if (s->precond < 0 || s->precond > QXD_PRECOND_DFL) return qxd_fail(ctx, QXD_EARG, "solve: unknown preconditioner");
     if (s->precond == QXD_PRECOND_SAP) QXD_TRY(sap_check(ctx));
+    if (s->precond == QXD_PRECOND_DFL && !ctx->fl[fl].dfl_basis)
+        return qxd_fail(ctx, QXD_ESTATE, "solve: deflation subspace not set up (qxd_dfl_setup)");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cbytes = (size_t)nrhs * ctx->g.V * 12 * 16;

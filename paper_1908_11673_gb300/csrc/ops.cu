@@ -90,14 +90,15 @@ int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z,
         QXD_CUDA(ctx, cudaMemcpyAsync(z, r, half_bytes(ctx, P), cudaMemcpyDeviceToDevice, st));
         return QXD_OK;
     }
-    if (kind == QXD_PRECOND_SAP) {
-        if (P == QXD_FP32) return sap_apply_even(ctx, fl, r, z, st);
+    if (kind == QXD_PRECOND_SAP || kind == QXD_PRECOND_DFL) {
+        auto even = kind == QXD_PRECOND_SAP ? sap_apply_even : dfl_apply_even;
+        if (P == QXD_FP32) return even(ctx, fl, r, z, st);
         void *r32, *z32;
         const size_t n = 12ull * ctx->g.Vh;
         QXD_TRY(qxd_ws(ctx, WS_PTC + 50, half_bytes(ctx, QXD_FP32), &r32));
         QXD_TRY(qxd_ws(ctx, WS_PTC + 51, half_bytes(ctx, QXD_FP32), &z32));
         QXD_TRY(blas_axpby(ctx, P, QXD_FP32, n, 1.0, 0.0, r, 0.0, 0.0, r32, st));
-        QXD_TRY(sap_apply_even(ctx, fl, r32, z32, st));
+        QXD_TRY(even(ctx, fl, r32, z32, st));
         return blas_axpby(ctx, QXD_FP32, P, n, 1.0, 0.0, z32, 0.0, 0.0, z, st);
     }
     if (kind == QXD_PRECOND_LEARNED) {

@@ -33,7 +33,14 @@ int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int n
 
 // SAP preconditioner (sap.cu): z_e = (M_SAP (r_e, 0))_e on FP32 internal even fields
 int sap_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st);
+// psi = M_SAP eta on full FP32 fields (even half, odd half; psi distinct from eta)
+int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStream_t st);
 int sap_check(qxd_ctx* ctx);
+
+// deflation (deflation.cu): out = M_dfl v on full FP32 fields (coarse GCR iterations and
+// residual reported if the pointers are given); z_e = (M_dfl (r_e, 0))_e on FP32 even fields
+int dfl_apply_full(qxd_ctx* ctx, int fl, const float4* v, float4* out, int* citers, double* crel, cudaStream_t st);
+int dfl_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st);
 
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,

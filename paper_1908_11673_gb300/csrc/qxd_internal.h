@@ -23,6 +23,12 @@ struct QxdFlavour {
     // learned preconditioner
     void* W = nullptr;         // device weights (complex float [layers][cout][cin][9][4][4])
     int nlayers = 0, nch = 0;
+    // deflation subspace (qxd_dfl_setup)
+    float4* dfl_basis = nullptr;  // [Ns] full FP32 fields, block-orthonormal
+    float2* dfl_A = nullptr;      // little operator [Nb][9][Ns][Ns]
+    int* dfl_nbr = nullptr;       // block neighbours [Nb][9]
+    int dfl_Ns = 0, dfl_cnmx = 0, dfl_cnkv = 0;
+    double dfl_ctol = 0.0;
 };
 
 struct qxd_ctx {
@@ -116,6 +122,7 @@ enum {
     WS_PTC = 192,
     WS_SAP = 272,
     WS_RAT = 288,
+    WS_DFL = 300,
     WS_NSLOTS = 320
 };
 

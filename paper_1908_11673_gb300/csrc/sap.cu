@@ -23,15 +23,16 @@
 #include <cmath>
 
 #include "blas.h"
+#include "block.cuh"
 #include "hop.cuh"
 #include "ops.h"
 #include "qxd_internal.h"
 
 namespace qxd {
 
-constexpr int kSapB = 4;          // block extent
-constexpr int kSapThreads = 128;  // half of the 4^4 block sites
-constexpr int kSapSites = 256;
+constexpr int kSapB = kBlk;
+constexpr int kSapThreads = kBlkThreads;
+constexpr int kSapSites = kBlkSites;
 
 struct SapDev {
     int nb[4];              // blocks per direction
@@ -44,12 +45,6 @@ struct SapDev {
     int nmr;
 };
 
-struct SiteRef {
-    int l[4];  // local coordinates in the block
-    int x[4];  // global coordinates
-    int h;     // half index of the site
-};
-
 // shared memory of one block: its links, two half-block spinor buffers and the
 // odd residual, all structure-of-arrays over the block's sites
 struct SapShared {
@@ -58,23 +53,6 @@ struct SapShared {
     float2 rho_o[12][kSapThreads];   // residual on the odd sites
     float red[3 * kSapThreads / 32];
 };
-
-// the t-th site of parity p in block bc
-__device__ __forceinline__ void block_site(const Geo& g, const int bc[4], int p, int t, SiteRef& s) {
-    int r = t;
-    const int x3h = r & 1;
-    r >>= 1;
-    s.l[2] = r & 3;
-    r >>= 2;
-    s.l[1] = r & 3;
-    s.l[0] = r >> 2;
-    s.l[3] = 2 * x3h + ((p + s.l[0] + s.l[1] + s.l[2]) & 1);
-    for (int mu = 0; mu < 4; ++mu) s.x[mu] = kSapB * bc[mu] + s.l[mu];
-    s.h = lex_index(g, s.x) >> 1;
-}
-
-// thread index of the local site l within its parity
-__device__ __forceinline__ int block_thread(const int l[4]) { return (((l[0] * 4 + l[1]) * 4 + l[2]) * 2) + (l[3] >> 1); }
 
 __device__ __forceinline__ void load_sm(const float2 (*sm)[kSapThreads], int t, cplx<float> s[12]) {
 #pragma unroll
@@ -223,15 +201,7 @@ __global__ void __launch_bounds__(kSapThreads) k_sap_sweep(Geo g, SapDev a, int 
     extern __shared__ __align__(16) unsigned char sap_smem[];
     SapShared& S = *reinterpret_cast<SapShared*>(sap_smem);
     int bc[4];
-    {
-        int b = blockIdx.x;
-        bc[3] = b % a.nb[3];
-        b /= a.nb[3];
-        bc[2] = b % a.nb[2];
-        b /= a.nb[2];
-        bc[1] = b % a.nb[1];
-        bc[0] = b / a.nb[1];
-    }
+    block_coords(blockIdx.x, a.nb, bc);
     if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) return;
     const int t = threadIdx.x;
     const int Vh = g.Vh;

@@ -18,7 +18,7 @@ LIBPATH = os.path.join(HERE, "libqxd.so")
 
 FP64, FP32, BF16 = 0, 1, 2
 CGNE, FGCR, MSCG = 0, 1, 2
-PRECOND_NONE, PRECOND_LEARNED, PRECOND_SAP = 0, 1, 2
+PRECOND_NONE, PRECOND_LEARNED, PRECOND_SAP, PRECOND_DFL = 0, 1, 2, 3
 
 STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: "QXD_ENAN",
           5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
@@ -27,6 +27,7 @@ EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_
            "qxd_apply_Dhat_eo", "qxd_apply_Dhat_eo_noalloc", "qxd_solve", "qxd_solve_multishift", "qxd_set_precond_weights",
            "qxd_set_sap", "qxd_sap_apply", "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
            "qxd_rat_apply", "qxd_pf_action", "qxd_rw_rat", "qxd_rw_rtm", "qxd_sdet",
+           "qxd_dfl_setup", "qxd_dfl_basis", "qxd_dfl_little", "qxd_dfl_apply",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -65,6 +66,11 @@ def rational(A, nu, mu):
                  mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     r._keep = (nu, mu)
     return r
+
+
+class DflParams(ctypes.Structure):
+    _fields_ = [("Ns", ctypes.c_int), ("ninv", ctypes.c_int), ("ctol", ctypes.c_double), ("cnmx", ctypes.c_int),
+                ("cnkv", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -113,6 +119,10 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_rw_rtm": (i, [vp, i, ctypes.POINTER(Rational), ctypes.POINTER(Rational), i, i,
                            ctypes.POINTER(Solver), vp, ctypes.POINTER(d), ctypes.POINTER(Info), vp]),
         "qxd_sdet": (i, [vp, i, ctypes.POINTER(d), ctypes.POINTER(i), vp]),
+        "qxd_dfl_setup": (i, [vp, i, ctypes.POINTER(DflParams), vp, vp]),
+        "qxd_dfl_basis": (i, [vp, i, i, vp, vp]),
+        "qxd_dfl_little": (i, [vp, i, vp, vp, ctypes.POINTER(i), vp]),
+        "qxd_dfl_apply": (i, [vp, i, vp, vp, ctypes.POINTER(Info), vp]),
         "qxd_profile": (i, [vp, i]),
         "qxd_profile_entry": (i, [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -280,6 +290,30 @@ class Context:
         nn = ctypes.c_int()
         self._check(self.lib.qxd_sdet(self._h, int(fl), ctypes.byref(ld), ctypes.byref(nn), _stream(stream)))
         return ld.value, nn.value
+
+    # ---- inexact deflation (DFL+SAP+GCR) ------------------------------------------
+    def dfl_setup(self, fl, seeds, Ns, ninv=2, ctol=1e-2, cnmx=64, cnkv=16, stream=None):
+        """Build the deflation subspace of flavour fl from seeds (complex64 [Ns][V][4][3])."""
+        p = DflParams(int(Ns), int(ninv), float(ctol), int(cnmx), int(cnkv))
+        self._check(self.lib.qxd_dfl_setup(self._h, int(fl), ctypes.byref(p), _ptr(seeds), _stream(stream)))
+
+    def dfl_basis(self, fl, k, out, stream=None):
+        self._check(self.lib.qxd_dfl_basis(self._h, int(fl), int(k), _ptr(out), _stream(stream)))
+
+    def dfl_little(self, fl, Ns, stream=None):
+        """(A [Nb][9][Ns][Ns] complex64 with A[B][s][l][k] = <phi_k|_B, D phi_l|_{B_s}>, nbr [Nb][9])."""
+        nb = ctypes.c_int()
+        self._check(self.lib.qxd_dfl_little(self._h, int(fl), None, None, ctypes.byref(nb), _stream(stream)))
+        A = np.empty((nb.value, 9, Ns, Ns), dtype=np.complex64)
+        nbr = np.empty((nb.value, 9), dtype=np.int32)
+        self._check(self.lib.qxd_dfl_little(self._h, int(fl), A.ctypes.data, nbr.ctypes.data, None,
+                                            _stream(stream)))
+        return A, nbr
+
+    def dfl_apply(self, fl, v, out, stream=None):
+        info = Info()
+        self._check(self.lib.qxd_dfl_apply(self._h, int(fl), _ptr(v), _ptr(out), ctypes.byref(info), _stream(stream)))
+        return info
 
     # ---- SAP preconditioner ----------------------------------------------------
     def set_sap(self, ncy=5, nmr=5):
