@@ -21,7 +21,8 @@ Reported:
              library copies eta in and psi out inside the timed call);
   cpu_baseline  the FP64 oracle applying D_w to a bounded sample of sites;
   next_rows  outside the timed region, on the same system: the SAP-preconditioned
-             solve (Sec. 4.4 SAP+GCR) against the unpreconditioned one, and the
+             solve (Sec. 4.4 SAP+GCR) and the deflated one (DFL+SAP+GCR, subspace
+             setup timed apart) against the unpreconditioned one, and the
              pseudofermion action of the printed degree-10 rational approximation
              (App. A.2: one 10-shift multi-shift CG plus FP64 assembly) and the
              small-determinant action (Sec. 2.2), each timed with CUDA events.
@@ -338,6 +339,21 @@ def run_native(args, w, name):
                 "sap_sweep_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
                 "sap_sweep_launches": blk["launches"] if blk else None,
                 "sap_sweep_GBps": blk["bytes"] / (blk["ms"] * 1e-3) / 1e9 if blk else None}
+        # inexact deflation (DFL+SAP+GCR): subspace from Ns Gaussian fields drawn on the
+        # device with a seeded generator, SAP(3,4) as smoother and for the inverse iteration
+        ctx.set_sap(3, 4)
+        gen = torch.Generator(device=dev).manual_seed(4242)
+        seeds = torch.randn((12, V, 4, 3), dtype=torch.complex64, device=dev, generator=gen)
+        torch.cuda.synchronize()
+        t0d = time.perf_counter()
+        ctx.dfl_setup(0, seeds, 12, ninv=2, ctol=1e-2, cnmx=64, stream=stream)
+        torch.cuda.synchronize()
+        dfl_setup_ms = (time.perf_counter() - t0d) * 1e3
+        del seeds
+        dkw = solve_kw | {"precond": qxd.PRECOND_DFL, "nkv": 16}
+        ms_dfl, inf_dfl = timed(lambda: ctx.solve(0, eta_d, psi_d, **dkw), 1)
+        nxt["dfl_fgcr_Ns12_ninv2_sap3_4"] = {"setup_ms": dfl_setup_ms, "ms": ms_dfl, "iters": inf_dfl[0].iters,
+                                              "true_relres": inf_dfl[0].true_relres}
         A_r, nu_r, mu_r = read_rational(GOLDEN_RATIONAL)
         rat = qxd.rational(A_r, nu_r, mu_r)
         phi_e = torch.from_numpy(np.ascontiguousarray(eta[: V // 2])).to(dev)

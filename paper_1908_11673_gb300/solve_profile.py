@@ -6,6 +6,11 @@ launch counts and CUDA-event time of every kernel class on its launching
 stream) and prints, per solve, the solver report and the kernel table.
 
     python -m paper_1908_11673_gb300.solve_profile --L 24,24,24,48 --precond sap [--ncy 5 --nmr 5]
+    python -m paper_1908_11673_gb300.solve_profile --L 24,24,24,48 --precond dfl --Ns 12 --ninv 2
+
+With --precond dfl the deflation subspace is built first (qxd_dfl_setup) from
+Ns Gaussian fields drawn on the device with a seeded torch generator; its
+setup time is printed.
 """
 from __future__ import annotations
 
@@ -20,14 +25,18 @@ from . import build, qxd, workload
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("--L", default="24,24,24,48", help="lattice extents x0,x1,x2,x3")
+    ap.add_argument("--L", default="24,24,24,48", help="physical lattice extents x0,x1,x2,x3")
     ap.add_argument("--cstar", type=int, default=0)
     ap.add_argument("--qhat", type=int, default=-2)
     ap.add_argument("--kappa", type=float, default=0.136377)
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--stout", type=int, default=5)
     ap.add_argument("--solver", choices=["fgcr", "cgne"], default="fgcr")
-    ap.add_argument("--precond", choices=["none", "sap"], default="none")
+    ap.add_argument("--precond", choices=["none", "sap", "dfl"], default="none")
+    ap.add_argument("--Ns", type=int, default=12)
+    ap.add_argument("--ninv", type=int, default=2)
+    ap.add_argument("--ctol", type=float, default=1e-2)
+    ap.add_argument("--cnmx", type=int, default=64)
     ap.add_argument("--ncy", type=int, default=5)
     ap.add_argument("--nmr", type=int, default=5)
     ap.add_argument("--nkv", type=int, default=16)
@@ -47,7 +56,17 @@ def main(argv=None):
     psi = torch.empty_like(eta)
     ctx.set_sap(args.ncy, args.nmr)
     kind = qxd.FGCR if args.solver == "fgcr" else qxd.CGNE
-    pre = qxd.PRECOND_SAP if args.precond == "sap" else qxd.PRECOND_NONE
+    pre = {"none": qxd.PRECOND_NONE, "sap": qxd.PRECOND_SAP, "dfl": qxd.PRECOND_DFL}[args.precond]
+    if args.precond == "dfl":
+        gen = torch.Generator(device="cuda").manual_seed(args.seed + 7)
+        seeds = torch.randn((args.Ns, ctx.V, 4, 3), dtype=torch.complex64, device="cuda", generator=gen)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.dfl_setup(0, seeds, args.Ns, ninv=args.ninv, ctol=args.ctol, cnmx=args.cnmx)
+        torch.cuda.synchronize()
+        print(json.dumps({"dfl_setup_ms": round((time.perf_counter() - t) * 1e3, 1), "Ns": args.Ns,
+                          "ninv": args.ninv}))
+        del seeds
     inner = qxd.FP32 if args.inner == "fp32" else qxd.BF16
     for _ in range(args.reps):
         ctx.profile(2)
