@@ -95,58 +95,78 @@ __device__ __forceinline__ void phase_mul(cplx<float> z, bool dag, Half<float>& 
 // spinor buffer nb.  HALO = false: hops leaving the block are dropped (block
 // operator).  HALO = true: they take the spinor of the neighbouring site from the
 // global field nb_glob (opposite parity) and, backwards, its link from global memory.
-template <int MU, bool HALO>
-__device__ __forceinline__ void hop_dir_sap(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
-                                            const float2 (*nb)[kSapThreads], const float4* nb_glob,
-                                            cplx<float> acc[12]) {
-    Half<float> hp, o;
-    Mat3<float> m;
-    cplx<float> z;
-    cplx<float> v[12];
-    const int sid = p * kSapThreads + block_thread(s.l);
-    if (s.l[MU] + 1 < kSapB || HALO) {
-        if (s.l[MU] + 1 < kSapB) {
-            int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
-            ln[MU] += 1;
-            load_sm(nb, block_thread(ln), v);
-        } else {
-            load_spinor<1>(nb_glob, g.Vh, neighbour_lex(g, s.x, MU, +1) >> 1, v);
-        }
-        project<MU, true>(v, hp);
-        link_sm(S, MU, sid, m, z);
-        mul_half<false>(m, hp, o);
-        phase_mul(z, false, o);
-        reconstruct<MU, true>(o, acc);
+// spin projection / reconstruction for the hop d = 2 mu + (0 forward, 1 backward),
+// chosen at run time
+__device__ __forceinline__ void project_rt(int d, const cplx<float> v[12], Half<float>& hp) {
+    switch (d) {
+        case 0: project<0, true>(v, hp); break;
+        case 1: project<0, false>(v, hp); break;
+        case 2: project<1, true>(v, hp); break;
+        case 3: project<1, false>(v, hp); break;
+        case 4: project<2, true>(v, hp); break;
+        case 5: project<2, false>(v, hp); break;
+        case 6: project<3, true>(v, hp); break;
+        default: project<3, false>(v, hp); break;
     }
-    if (s.l[MU] > 0 || HALO) {
-        if (s.l[MU] > 0) {
-            int ln[4] = {s.l[0], s.l[1], s.l[2], s.l[3]};
-            ln[MU] -= 1;
-            const int tn = block_thread(ln);
-            load_sm(nb, tn, v);
-            link_sm(S, MU, (1 - p) * kSapThreads + tn, m, z);
-        } else {
-            const int hn = neighbour_lex(g, s.x, MU, -1) >> 1;
-            load_spinor<1>(nb_glob, g.Vh, hn, v);
-            load_link32(a.U32[1 - p], a.Z32[1 - p], g.Vh, MU, hn, m, z);
-        }
-        project<MU, false>(v, hp);
-        mul_half<true>(m, hp, o);
-        phase_mul(z, true, o);
-        reconstruct<MU, false>(o, acc);
+}
+__device__ __forceinline__ void reconstruct_rt(int d, const Half<float>& o, cplx<float> acc[12]) {
+    switch (d) {
+        case 0: reconstruct<0, true>(o, acc); break;
+        case 1: reconstruct<0, false>(o, acc); break;
+        case 2: reconstruct<1, true>(o, acc); break;
+        case 3: reconstruct<1, false>(o, acc); break;
+        case 4: reconstruct<2, true>(o, acc); break;
+        case 5: reconstruct<2, false>(o, acc); break;
+        case 6: reconstruct<3, true>(o, acc); break;
+        default: reconstruct<3, false>(o, acc); break;
     }
 }
 
-// out = -1/2 sum_mu [...] at site s of parity p (block operator, or with the halo)
+// out = -1/2 sum_mu [(1 - gamma_mu) V(x,mu) f(x+mu) + (1 + gamma_mu) V(x-mu,mu)^+ f(x-mu)]
+// at site s of parity p, f the opposite-parity spinors in the buffer nb.
+// HALO = false: hops leaving the block are dropped (block operator).  HALO = true:
+// they take the spinor of the neighbouring site from the global field nb_glob
+// (opposite parity) and, backwards, its link from global memory.
+// The eight hops run as one loop with the direction chosen at run time, so the
+// colour multiplication exists once in the code: the sweep calls this six times,
+// and fully unrolled copies overflow the instruction cache.
 template <bool HALO>
 __device__ __forceinline__ void hop_sap(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
                                         const float2 (*nb)[kSapThreads], const float4* nb_glob, cplx<float> out[12]) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = {0.f, 0.f};
-    hop_dir_sap<0, HALO>(g, a, S, s, p, nb, nb_glob, out);
-    hop_dir_sap<1, HALO>(g, a, S, s, p, nb, nb_glob, out);
-    hop_dir_sap<2, HALO>(g, a, S, s, p, nb, nb_glob, out);
-    hop_dir_sap<3, HALO>(g, a, S, s, p, nb, nb_glob, out);
+    const int t = block_thread(s.l);
+    const int sid = p * kSapThreads + t;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+        const int mu = d >> 1;
+        const bool fwd = (d & 1) == 0;
+        const int lmu = mu == 0 ? s.l[0] : mu == 1 ? s.l[1] : mu == 2 ? s.l[2] : s.l[3];
+        const bool inside = fwd ? lmu + 1 < kSapB : lmu > 0;
+        if (!inside && !HALO) continue;
+        cplx<float> v[12];
+        Mat3<float> m;
+        cplx<float> z;
+        if (inside) {
+            // thread index of the neighbour within its parity
+            const int l3 = s.l[3];
+            const int step = mu == 0 ? 32 : mu == 1 ? 8 : mu == 2 ? 2 : 0;
+            const int tn = mu < 3 ? (fwd ? t + step : t - step) : (fwd ? t + (l3 & 1) : t - ((l3 & 1) ^ 1));
+            load_sm(nb, tn, v);
+            link_sm(S, mu, fwd ? sid : (1 - p) * kSapThreads + tn, m, z);
+        } else {
+            const int hn = neighbour_lex(g, s.x, mu, fwd ? +1 : -1) >> 1;
+            load_spinor<1>(nb_glob, g.Vh, hn, v);
+            if (fwd) link_sm(S, mu, sid, m, z);
+            else load_link32(a.U32[1 - p], a.Z32[1 - p], g.Vh, mu, hn, m, z);
+        }
+        Half<float> hp, o;
+        project_rt(d, v, hp);
+        if (fwd) mul_half<false>(m, hp, o);
+        else mul_half<true>(m, hp, o);
+        phase_mul(z, !fwd, o);
+        reconstruct_rt(d, o, out);
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) out[k] = -0.5f * out[k];
 }
