@@ -406,8 +406,13 @@ def run_native(args, w, name):
                         "share": round(p["ms"] / total_ms_k, 4) if total_ms_k else None,
                         "GB/s": round(gbs, 1) if gbs else None})
     info = infos[-1]
+    # the mixed solver's outer residual runs in double-float; check the last solution in FP64
+    dpsi = torch.empty_like(psi_d)
+    ctx.apply_Dw(0, qxd.FP64, psi_d, dpsi, stream=stream)
+    torch.cuda.synchronize()
+    rel64 = float(torch.linalg.vector_norm(eta_d - dpsi) / torch.linalg.vector_norm(eta_d))
     tts = {"mixed_ms": ms / args.steps, "iters_inner": info.iters, "outer_restarts": info.restarts,
-           "true_relres": info.true_relres, "status": info.status}
+           "true_relres": info.true_relres, "true_relres_fp64_check": rel64, "status": info.status}
     if base:
         tts.update(base)
         tts["speedup_vs_fp64_cgne"] = base["fp64_cgne_ms"] / (ms / args.steps)

@@ -58,7 +58,11 @@ typedef enum {
     QXD_ESTATE = 7       /* call out of order (e.g. operator before set_links/set_clover) */
 } qxd_status;
 
-typedef enum { QXD_FP64 = 0, QXD_FP32 = 1, QXD_BF16 = 2 } qxd_prec;
+/* QXD_DF64: FP64 data (complex128 at the interface) with double-float arithmetic
+ * (each real an unevaluated sum of two floats, about 48 significant bits) on the
+ * FP32 pipe; qxd_apply_Dw only (one right-hand side), and the outer residual of
+ * the FGCR solver. */
+typedef enum { QXD_FP64 = 0, QXD_FP32 = 1, QXD_BF16 = 2, QXD_DF64 = 3 } qxd_prec;
 
 typedef enum { QXD_CGNE = 0, QXD_FGCR = 1, QXD_MSCG = 2 } qxd_solver_kind;
 
@@ -113,8 +117,10 @@ typedef struct {
     int precond;
 } qxd_solver;
 
-/* Solver report.  true_relres is always recomputed in FP64 from the returned
- * solution.  op_applies counts applications of Dhat (or D) in any precision. */
+/* Solver report.  true_relres is always recomputed from the returned solution with
+ * the FP64 operator data: in FP64 arithmetic for CGNE and for FGCR with FP64 inner
+ * solves, in double-float arithmetic (QXD_DF64, about 48-bit significands) for the
+ * mixed-precision FGCR.  op_applies counts applications of Dhat (or D) in any precision. */
 typedef struct {
     int status;
     int iters;
@@ -154,7 +160,8 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream);
 /* out = D in on the full simulated lattice (eq. dirac with dD_b = 0), for nrhs
  * right-hand sides.  in, out: [nrhs][V][4][3] complex128 (prec = QXD_FP64) or
  * complex64 (QXD_FP32, and QXD_BF16 which stores spinors in bfloat16 inside the
- * kernel and accumulates in FP32).  in and out must not overlap. */
+ * kernel and accumulates in FP32); QXD_DF64: complex128 like QXD_FP64, arithmetic in
+ * double-float, nrhs = 1.  in and out must not overlap. */
 int qxd_apply_Dw(qxd_ctx* ctx, int fl, int prec, const void* in, void* out, int nrhs, void* stream);
 
 /* out_e = Dhat in_e = (D_ee - D_eo D_oo^-1 D_oe) in_e (Sec. 2.2) on even-site

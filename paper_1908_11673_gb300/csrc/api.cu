@@ -137,7 +137,9 @@ static void free_flavour(QxdFlavour& F) {
     for (int k = 0; k < 2; ++k) {
         cudaFree(F.C64[k]);
         cudaFree(F.C32[k]);
+        cudaFree(F.Cdf[k]);
     }
+    cudaFree(F.Vdf);
     cudaFree(F.W);
     cudaFree(F.dfl_basis);
     cudaFree(F.dfl_A);
@@ -247,7 +249,10 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
                   cudaMalloc(&F.C64[0], 2 * 36 * Vh * sizeof(double2)) == cudaSuccess &&
                   cudaMalloc(&F.C64[1], 2 * 36 * Vh * sizeof(double2)) == cudaSuccess &&
                   cudaMalloc(&F.C32[0], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&F.C32[1], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess;
+                  cudaMalloc(&F.C32[1], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&F.Vdf, 2 * 36 * Vh * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&F.Cdf[0], 2 * 36 * Vh * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&F.Cdf[1], 2 * 36 * Vh * sizeof(float4)) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             free_flavour(F);
@@ -271,11 +276,12 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
 
 int qxd_apply_Dw(qxd_ctx* ctx, int fl, int prec, const void* in, void* out, int nrhs, void* stream) {
     QXD_TRY(check_fl(ctx, fl));
-    if (prec < 0 || prec > 2) return qxd_fail(ctx, QXD_EARG, "apply_Dw: precision must be 0, 1 or 2");
+    if (prec < 0 || prec > 3) return qxd_fail(ctx, QXD_EARG, "apply_Dw: precision must be 0, 1, 2 or 3");
     if (nrhs < 1 || !in || !out) return qxd_fail(ctx, QXD_EARG, "apply_Dw: bad arguments");
+    if (prec == QXD_DF64 && nrhs != 1) return qxd_fail(ctx, QXD_EARG, "apply_Dw: QXD_DF64 takes one right-hand side");
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const int cprec = prec == QXD_FP64 ? 0 : 1;
+    const int cprec = (prec == QXD_FP64 || prec == QXD_DF64) ? 0 : 1;
     const size_t cbytes = (size_t)nrhs * ctx->g.V * 12 * (cprec == 0 ? 16 : 8);
     const void* din;
     void* dout;
@@ -288,11 +294,21 @@ int qxd_apply_Dw(qxd_ctx* ctx, int fl, int prec, const void* in, void* out, int 
     QXD_TRY(qxd_ws(ctx, WS_T1, hb, &io));
     QXD_TRY(qxd_ws(ctx, WS_T2, hb, &oe));
     QXD_TRY(qxd_ws(ctx, WS_T3, hb, &oo));
-    QXD_TRY(launch_pack(ctx, cprec, din, 1, 0, prec, ie, nrhs, st));
-    QXD_TRY(launch_pack(ctx, cprec, din, 1, 1, prec, io, nrhs, st));
+    // double-float: FP64 layout converted in place (the two layouts share their 16-byte chunks)
+    const int iprec = prec == QXD_DF64 ? QXD_FP64 : prec;
+    QXD_TRY(launch_pack(ctx, cprec, din, 1, 0, iprec, ie, nrhs, st));
+    QXD_TRY(launch_pack(ctx, cprec, din, 1, 1, iprec, io, nrhs, st));
+    if (prec == QXD_DF64) {
+        QXD_TRY(blas_split_df64(ctx, ie, ie, 12ull * ctx->g.Vh, st));
+        QXD_TRY(blas_split_df64(ctx, io, io, 12ull * ctx->g.Vh, st));
+    }
     QXD_TRY(op_Dw(ctx, fl, prec, Full{ie, io}, Full{oe, oo}, st, nrhs));
-    QXD_TRY(launch_unpack(ctx, prec, oe, 0, cprec, dout, 1, nrhs, st));
-    QXD_TRY(launch_unpack(ctx, prec, oo, 1, cprec, dout, 1, nrhs, st));
+    if (prec == QXD_DF64) {
+        QXD_TRY(blas_join_df64(ctx, oe, oe, 12ull * ctx->g.Vh, st));
+        QXD_TRY(blas_join_df64(ctx, oo, oo, 12ull * ctx->g.Vh, st));
+    }
+    QXD_TRY(launch_unpack(ctx, iprec, oe, 0, cprec, dout, 1, nrhs, st));
+    QXD_TRY(launch_unpack(ctx, iprec, oo, 1, cprec, dout, 1, nrhs, st));
     return finish_out(ctx, out, dout, cbytes, host_out, st);
 }
 

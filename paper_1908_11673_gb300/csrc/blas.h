@@ -29,6 +29,11 @@ struct MultiCoef {
 int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* b, int slot, cudaStream_t st);
 // result[slot] = |a|^2 over finite entries, result[slot+1] = number of non-finite entries
 int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st);
+// Double-float conversions over n complex numbers (16-byte chunks): FP64 -> double-float
+// (in == out allowed), double-float -> FP64 (in == out allowed), r = eta - dx (dx double-float)
+int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
+int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
+int blas_residual_df64(qxd_ctx* ctx, const void* eta, const void* dx, void* r, size_t n, cudaStream_t st);
 // result[slot] = sum of the finite entries of the real FP64 array a[n], result[slot+1] = count of the others
 int blas_sum_real(qxd_ctx* ctx, const double* a, size_t n, int slot, cudaStream_t st);
 // result[slot + 2j], [slot + 2j + 1] = <W_j, v>, j < k

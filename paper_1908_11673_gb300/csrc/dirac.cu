@@ -12,13 +12,13 @@
 
 namespace qxd {
 
-static const char* prec_name(int P) { return P == 0 ? "fp64" : (P == 1 ? "fp32" : "bf16"); }
-static double spinor_bytes(int P) { return P == 0 ? 192.0 : (P == 1 ? 96.0 : 48.0); }
-static double link_bytes(int P) { return P == 0 ? 144.0 : 56.0; }   // V (FP64) or 2 rows of U + z (FP32)
-static double diag_bytes(int P) { return P == 0 ? 576.0 : 288.0; }
+static const char* prec_name(int P) { return P == 0 ? "fp64" : (P == 1 ? "fp32" : (P == 2 ? "bf16" : "df64")); }
+static double spinor_bytes(int P) { return (P == 0 || P == 3) ? 192.0 : (P == 1 ? 96.0 : 48.0); }
+static double link_bytes(int P) { return (P == 0 || P == 3) ? 144.0 : 56.0; }   // V (FP64) or 2 rows of U + z (FP32)
+static double diag_bytes(int P) { return (P == 0 || P == 3) ? 576.0 : 288.0; }
 
 template <int P, int SELF, int POST>
-__global__ void __launch_bounds__(kThreads) k_hop(Geo g, HopDev a) {
+__global__ void __launch_bounds__(kThreads, (P == 3 ? 4 : 1)) k_hop(Geo g, HopDev a) {
     using R = typename Prec<P>::real;
     using CH = typename Prec<P>::chunk;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -46,15 +46,20 @@ __global__ void __launch_bounds__(kThreads) k_hop(Geo g, HopDev a) {
         }
         if constexpr (SELF == 1) {
             R d[72];
-            load_diag<P == 0 ? 0 : 1>(a.diag, g.Vh, h, d);
+            load_diag<P == 0 ? 0 : (P == 3 ? 3 : 1)>(a.diag, g.Vh, h, d);
             apply_diag(d, s);
         }
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = acc[k] + s[k];
     }
     if constexpr (POST == 1) {
+        if constexpr (P == 3) {
+            // the lazy double-float sums are renormalised before they become factors
+#pragma unroll
+            for (int k = 0; k < 12; ++k) acc[k] = {df_norm(acc[k].re), df_norm(acc[k].im)};
+        }
         R d[72];
-        load_diag<P == 0 ? 0 : 1>(a.diaginv, g.Vh, h, d);
+        load_diag<P == 0 ? 0 : (P == 3 ? 3 : 1)>(a.diaginv, g.Vh, h, d);
         apply_diag(d, acc);
     }
     if (a.g5_out) {
@@ -113,6 +118,8 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
     d.out = a.out;
     d.V64_out = F.V64 + (size_t)po * 36 * Vh;
     d.V64_in = F.V64 + (size_t)pi * 36 * Vh;
+    d.Vdf_out = F.Vdf + (size_t)po * 36 * Vh;
+    d.Vdf_in = F.Vdf + (size_t)pi * 36 * Vh;
     d.U32_out = ctx->U32 + (size_t)po * 12 * Vh;
     d.U32_in = ctx->U32 + (size_t)pi * 12 * Vh;
     d.Z32_out = F.Z32 + (size_t)po * 2 * Vh;
@@ -120,6 +127,9 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
     if (prec == QXD_FP64) {
         d.diag = F.C64[0] + (size_t)po * 36 * Vh;
         d.diaginv = F.C64[1] + (size_t)po * 36 * Vh;
+    } else if (prec == QXD_DF64) {
+        d.diag = F.Cdf[0] + (size_t)po * 36 * Vh;
+        d.diaginv = F.Cdf[1] + (size_t)po * 36 * Vh;
     } else {
         d.diag = F.C32[0] + (size_t)po * 18 * Vh;
         d.diaginv = F.C32[1] + (size_t)po * 18 * Vh;
@@ -132,8 +142,8 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
     // site-diagonal terms once, spinors (neighbour, self, output) once per right-hand side
     char name[48];
     // FP32 and BF16 go through the autotuned multi-right-hand-side kernel (also
-    // for one right-hand side); FP64 keeps the one-site-per-thread kernel
-    const bool mr = prec != QXD_FP64;
+    // for one right-hand side); FP64 and double-float keep the one-site-per-thread kernel
+    const bool mr = prec == QXD_FP32 || prec == QXD_BF16;
     std::snprintf(name, sizeof name, "hop_%s_self%d_post%d%s", prec_name(prec), a.self_mode, a.post_mode,
                   a.nrhs > 1 ? "_mrhs" : "");
     const double per_rhs = spinor_bytes(prec) * (2 + (a.self_mode ? 1 : 0));
@@ -144,6 +154,7 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
         return launch_hop_mr(ctx, prec, d, a, st, &nr);
     }
     if (prec == QXD_FP64) launch_hop_p<0>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
+    else if (prec == QXD_DF64) launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
     else if (prec == QXD_FP32) launch_hop_p<1>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
     else launch_hop_p<2>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
     QXD_CUDA(ctx, cudaGetLastError());

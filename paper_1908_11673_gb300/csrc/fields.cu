@@ -1,6 +1,7 @@
 // Field set-up kernels: gauge-field ingest with the C* mirror fill, per-flavour
 // hopping phases, and the site-diagonal term 1/(2 kappa) + dD_sw with its
 // inverse (Sec. 2.1 eq. cstar-bc-gauge; Sec. 2.2 eqs. frw-covder, sw-term).
+#include "blas.h"
 #include "qxd_internal.h"
 
 namespace qxd {
@@ -352,6 +353,10 @@ int launch_set_flavour(qxd_ctx* ctx, int fl, cudaStream_t st) {
                                   F.C32[0], F.C64[1], F.C32[1], ctx->dev_flag);
     }
     QXD_CUDA(ctx, cudaGetLastError());
+    // double-float copies of the FP64 links and site-diagonal terms (outer residual)
+    QXD_TRY(blas_split_df64(ctx, F.V64, F.Vdf, 2ull * 36 * g.Vh, st));
+    QXD_TRY(blas_split_df64(ctx, F.C64[0], F.Cdf[0], 2ull * 36 * g.Vh, st));
+    QXD_TRY(blas_split_df64(ctx, F.C64[1], F.Cdf[1], 2ull * 36 * g.Vh, st));
     int flag = 0;
     QXD_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));

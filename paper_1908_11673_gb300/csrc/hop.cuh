@@ -77,6 +77,17 @@ QXD_HD void load_link64(const double2* __restrict__ V64, int Vh, int mu, int h, 
         }
 }
 
+// double-float copy of the FP64 links (one float4 per complex entry)
+QXD_HD void load_link_df(const float4* __restrict__ Vdf, int Vh, int mu, int h, Mat3<dfl>& m) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float4 v = QXD_LDG(Vdf + (size_t)(mu * 9 + i * 3 + j) * Vh + h);
+            m.a[i][j] = {dfl(v.x, v.y), dfl(v.z, v.w)};
+        }
+}
+
 // FP32: two rows of U, third row = conj(row0 x row1), then the phase z
 QXD_HD void load_link32(const float4* __restrict__ U32, const float4* __restrict__ Z32, int Vh, int mu, int h,
                         Mat3<float>& m, cplx<float>& z) {
@@ -126,6 +137,8 @@ struct HopDev {
     // links of the output parity (forward) and of the input parity (backward)
     const double2* V64_out;
     const double2* V64_in;
+    const float4* Vdf_out;  // double-float copies of V64 (precision 3)
+    const float4* Vdf_in;
     const float4* U32_out;
     const float4* U32_in;
     const float4* Z32_out;
@@ -155,6 +168,9 @@ QXD_HD void hop_dir(const Geo& g, const HopDev& a, const typename Prec<P>::chunk
     if constexpr (P == 0) {
         load_link64(a.V64_out, Vh, MU, h, m);
         mul_half<false>(m, hp, r);
+    } else if constexpr (P == 3) {
+        load_link_df(a.Vdf_out, Vh, MU, h, m);
+        mul_half<false>(m, hp, r);
     } else {
         cplx<float> z;
         load_link32(a.U32_out, a.Z32_out, Vh, MU, h, m, z);
@@ -174,6 +190,9 @@ QXD_HD void hop_dir(const Geo& g, const HopDev& a, const typename Prec<P>::chunk
     project<MU, false>(s, hp);
     if constexpr (P == 0) {
         load_link64(a.V64_in, Vh, MU, nb, m);
+        mul_half<true>(m, hp, r);
+    } else if constexpr (P == 3) {
+        load_link_df(a.Vdf_in, Vh, MU, nb, m);
         mul_half<true>(m, hp, r);
     } else {
         cplx<float> z;

@@ -7,7 +7,7 @@
 namespace qxd {
 
 size_t half_bytes(const qxd_ctx* ctx, int P) {
-    const size_t per = (P == QXD_FP64) ? 192 : (P == QXD_FP32 ? 96 : 48);
+    const size_t per = (P == QXD_FP64 || P == QXD_DF64) ? 192 : (P == QXD_FP32 ? 96 : 48);
     return per * (size_t)ctx->g.Vh;
 }
 

@@ -30,6 +30,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include "df64.cuh"
+
 #define QXD_HD __host__ __device__ __forceinline__
 
 #ifdef __CUDA_ARCH__
@@ -157,6 +159,10 @@ template <int P> struct Prec;
 template <> struct Prec<0> { using real = double; using chunk = double2; static constexpr int nchunk = 12; };
 template <> struct Prec<1> { using real = float;  using chunk = float4;  static constexpr int nchunk = 6; };
 template <> struct Prec<2> { using real = float;  using chunk = uint4;   static constexpr int nchunk = 3; };
+// FP64 data held as double-float pairs, arithmetic in double-float on the FP32 pipe:
+// a complex number is one float4 {re.hi, re.lo, im.hi, im.lo}, the chunk of 16
+// bytes that the FP64 layout uses for one complex128
+template <> struct Prec<3> { using real = dfl;    using chunk = float4;  static constexpr int nchunk = 12; };
 
 template <int P>
 QXD_HD void load_spinor(const typename Prec<P>::chunk* __restrict__ base, int stride, int h,
@@ -173,6 +179,12 @@ QXD_HD void load_spinor(const typename Prec<P>::chunk* __restrict__ base, int st
             float4 v = QXD_LDG(base + (size_t)c * stride + h);
             s[2 * c] = {v.x, v.y};
             s[2 * c + 1] = {v.z, v.w};
+        }
+    } else if constexpr (P == 3) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            float4 v = QXD_LDG(base + (size_t)k * stride + h);
+            s[k] = {dfl(v.x, v.y), dfl(v.z, v.w)};
         }
     } else {
 #pragma unroll
@@ -196,6 +208,12 @@ QXD_HD void store_spinor(typename Prec<P>::chunk* __restrict__ base, int stride,
 #pragma unroll
         for (int c = 0; c < 6; ++c)
             base[(size_t)c * stride + h] = make_float4(s[2 * c].re, s[2 * c].im, s[2 * c + 1].re, s[2 * c + 1].im);
+    } else if constexpr (P == 3) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dfl re = df_norm(s[k].re), im = df_norm(s[k].im);
+            base[(size_t)k * stride + h] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
     } else {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -243,6 +261,14 @@ QXD_HD void load_diag(const void* __restrict__ base, int stride, int h, typename
             double2 v = QXD_LDG(b + (size_t)k * stride + h);
             a[2 * k] = v.x;
             a[2 * k + 1] = v.y;
+        }
+    } else if constexpr (P == 3) {
+        const float4* b = static_cast<const float4*>(base);
+#pragma unroll
+        for (int k = 0; k < 36; ++k) {
+            float4 v = QXD_LDG(b + (size_t)k * stride + h);
+            a[2 * k] = dfl(v.x, v.y);
+            a[2 * k + 1] = dfl(v.z, v.w);
         }
     } else {
         const float4* b = static_cast<const float4*>(base);

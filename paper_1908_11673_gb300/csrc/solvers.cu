@@ -30,14 +30,30 @@ static int status_of_norm(qxd_ctx* ctx, double nonfinite, const char* where) {
 }
 
 // ---------------------------------------------------------------------------
-// r = eta - D x (FP64, full lattice); returns |r|^2 in *rr
+// r = eta - D x (FP64 data, full lattice); returns |r|^2 in *rr.  df: D x in
+// double-float arithmetic on the FP32 pipe (about 48-bit significands; the
+// FP64 pipe of this GPU runs at 1/64 of the FP32 rate), else in FP64.
 int full_residual64(qxd_ctx* ctx, int fl, const Full& eta, const Full& x, const Full& r, const Full& tmp_o,
-                    double* rr, cudaStream_t st) {
+                    double* rr, cudaStream_t st, bool df) {
     const size_t n = 12ull * ctx->g.Vh;
-    // r = D x, then r = eta - r
-    QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, r, st));
-    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.e, -1.0, 0.0, r.e, st));
-    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.o, -1.0, 0.0, r.o, st));
+    if (df) {
+        const size_t hb = half_bytes(ctx, QXD_FP64);
+        void *xe, *xo, *de, *dO;
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 124, hb, &xe));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 125, hb, &xo));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 126, hb, &de));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 127, hb, &dO));
+        QXD_TRY(blas_split_df64(ctx, x.e, xe, n, st));
+        QXD_TRY(blas_split_df64(ctx, x.o, xo, n, st));
+        QXD_TRY(op_Dw(ctx, fl, QXD_DF64, Full{xe, xo}, Full{de, dO}, st));
+        QXD_TRY(blas_residual_df64(ctx, eta.e, de, r.e, n, st));
+        QXD_TRY(blas_residual_df64(ctx, eta.o, dO, r.o, n, st));
+    } else {
+        // r = D x, then r = eta - r
+        QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, r, st));
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.e, -1.0, 0.0, r.e, st));
+        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.o, -1.0, 0.0, r.o, st));
+    }
     QXD_TRY(blas_norm2(ctx, 0, n, r.e, 0, st));
     QXD_TRY(blas_norm2(ctx, 0, n, r.o, 2, st));
     QXD_TRY(blas_fetch(ctx, 4, st));
@@ -129,7 +145,7 @@ int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, con
         QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.e, 1.0, 0.0, x.e, st));
         QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.o, 1.0, 0.0, x.o, st));
         double rr;
-        QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{to, to}, &rr, st));
+        QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{to, to}, &rr, st, false));
         info->op_applies += 1;
         info->true_relres = std::sqrt(rr) / enorm;
         if (info->true_relres <= s->tol) return QXD_OK;
@@ -366,7 +382,7 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     for (int outer = 0; outer < 64; ++outer) {
         if (outer > 0) {
             double rr;
-            QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
+            QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st, P != QXD_FP64));
             info->op_applies += 1;
             relres = std::sqrt(rr) / enorm;
             info->true_relres = relres;
@@ -406,7 +422,7 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
     }
     double rr;
-    QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
+    QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st, P != QXD_FP64));
     info->true_relres = std::sqrt(rr) / enorm;
     if (info->true_relres <= s->tol) return QXD_OK;
     return qxd_fail(ctx, QXD_ENOCONV, "FGCR: tolerance not reached within nmx");

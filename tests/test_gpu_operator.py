@@ -6,7 +6,9 @@ Tolerances (norm-relative over the whole output):
                     binary32 (2^-24 relative each) and each output component sums
                     ~10^2 products of O(1) terms; observed errors are a few 1e-7;
   BF16 spinors      2e-2: input and output spinors are rounded to bfloat16
-                    (2^-9 relative), the arithmetic is FP32.
+                    (2^-9 relative), the arithmetic is FP32;
+  DF64              1e-12: FP64 data in double-float arithmetic, each real held to
+                    2^-48 relative and each output component a sum of ~10^2 products.
 """
 import numpy as np
 import pytest
@@ -25,15 +27,15 @@ GEOMS = [
     ((4, 6, 4, 4), 3, (np.pi, 0.0, 0.0, 0.0), 1),
     ((8, 8, 8, 8), 0, (np.pi, 0.0, 0.0, 0.0), -2),
 ]
-TOL = {0: 1e-13, 1: 2e-6, 2: 2e-2}
+TOL = {0: 1e-13, 1: 2e-6, 2: 2e-2, 3: 1e-12}
 
 
 @pytest.mark.parametrize("L,cstar,theta,qhat", GEOMS)
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_apply_Dw_parity(L, cstar, theta, qhat, prec):
     qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=qhat, seed=1000 + sum(L))
     psi = workload.spinor(op.geom.V, 5)
-    if prec != 0:
+    if prec in (1, 2):
         psi = psi.astype(np.complex64)
     out = np.empty_like(psi)
     ctx.apply_Dw(0, prec, psi, out)
@@ -92,6 +94,8 @@ def test_full_size_sampled_parity():
     ctx.apply_Dw(0, 0, d_in, d_out)
     out = d_out.cpu().numpy()
     assert relerr(out[sites], ref) <= 1e-13
+    ctx.apply_Dw(0, 3, d_in, d_out)
+    assert relerr(d_out.cpu().numpy()[sites], ref) <= TOL[3]
     d_in32 = d_in.to(torch.complex64)
     d_out32 = torch.empty_like(d_in32)
     ctx.apply_Dw(0, 1, d_in32, d_out32)

@@ -54,3 +54,19 @@ def test_solver_failures_are_reported():
         ctx.apply_Dw(3, 0, eta, psi)  # flavour slot never set
     assert e.value.code == 7
     ctx.close()
+
+
+def test_mixed_fgcr_residual_certified_in_fp64():
+    """The mixed solver takes its outer residual with the FP64 data in double-float
+    arithmetic; an FP64 residual of the returned solution agrees with its report."""
+    qxd, ctx, op, _, _ = setup((8, 8, 8, 8), 0, (np.pi, 0, 0, 0), qhat=-2, seed=5600, stout=2)
+    eta = workload.spinor(op.geom.V, 5601)
+    psi = np.empty_like(eta)
+    info = ctx.solve(0, eta, psi, kind=1, tol=1e-10, inner=1, nkv=16)
+    assert info.status == 0 and info.true_relres <= 1e-10
+    dpsi = np.empty_like(psi)
+    ctx.apply_Dw(0, 0, psi, dpsi)
+    rel64 = np.linalg.norm(eta - dpsi) / np.linalg.norm(eta)
+    assert rel64 <= 1e-10
+    assert abs(rel64 - info.true_relres) <= 1e-3 * rel64
+    ctx.close()
