@@ -470,6 +470,23 @@ __global__ void k_axpby(size_t nch, double ar, double ai, const void* __restrict
     }
 }
 
+// z = x + a*w (same precision, z distinct from x and w)
+template <int P>
+__global__ void k_axpy3(size_t nch, double ar, double ai, const void* __restrict__ w, const void* __restrict__ x,
+                        void* __restrict__ z) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    const cplx<R> a = {(R)ar, (R)ai};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> xv[NC], wv[NC];
+        Chunk<P>::ld(x, i, xv);
+        Chunk<P>::ld(w, i, wv);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cmac(xv[c], a, wv[c]);
+        Chunk<P>::st(z, i, xv);
+    }
+}
+
 // y = a*x + b*y between two precisions, site by site (grid: sites x fields)
 template <int PX, int PY>
 __global__ void k_axpby_site(int Vh, double ar, double ai, const void* __restrict__ x, double br, double bi,
@@ -577,6 +594,18 @@ int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, con
         else QXD_AXPBY(2, 1);
 #undef QXD_AXPBY
     }
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+int blas_axpy3(qxd_ctx* ctx, int p, size_t n, double ar, double ai, const void* w, const void* x, void* z,
+               cudaStream_t st) {
+    ProfScope prof(ctx, "axpy3", (double)n * eb(p) * 3, st);
+    const size_t nc = nchunks(p, n);
+    const int nb = upd_blocks(ctx, nc);
+    if (p == 0) k_axpy3<0><<<nb, 256, 0, st>>>(nc, ar, ai, w, x, z);
+    else if (p == 1) k_axpy3<1><<<nb, 256, 0, st>>>(nc, ar, ai, w, x, z);
+    else k_axpy3<2><<<nb, 256, 0, st>>>(nc, ar, ai, w, x, z);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }

@@ -42,6 +42,9 @@ int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, c
 // y = a x + b y
 int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, const void* x, double br, double bi,
                void* y, cudaStream_t st);
+// z = x + a w (same precision, out of place)
+int blas_axpy3(qxd_ctx* ctx, int p, size_t n, double ar, double ai, const void* w, const void* x, void* z,
+               cudaStream_t st);
 // y += sum_j c_j X_j  (px == py)
 int blas_multi_axpy(qxd_ctx* ctx, int px, int py, size_t n, int k, const double* cre, const double* cim,
                     const void* const* X, void* y, cudaStream_t st);

@@ -255,16 +255,22 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
     std::vector<double> Rre(nkv * nkv), Rim(nkv * nkv), are(nkv), aim(nkv), ww(nkv), cre(nkv), cim(nkv);
     std::vector<const void*> Wc(nkv + 1);
     bool done = false;
+    // Without a preconditioner the search direction of step k is the residual r_k
+    // itself: it is kept in Z[k], and the update r_{k+1} = r_k - a_k w_k is written
+    // straight into Z[k+1] (one copy of r per cycle instead of one per step).
+    const bool rz = !split && s->precond == QXD_PRECOND_NONE;
     while (!done && *iters < max_iter) {
         int K = 0;
         const double rr_cycle = rr;
+        if (rz) QXD_CUDA(ctx, cudaMemcpyAsync(Z[0], r, hbb, cudaMemcpyDeviceToDevice, st));
         for (int k = 0; k < nkv; ++k) {
-            QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, r, Z[k], ztmp, st));
+            if (!rz) QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, r, Z[k], ztmp, st));
+            const void* rk = rz ? Z[k] : r;  // current residual
             QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Z[k], W[k], to, st));
             // <W_j, w_k> for j < k and <r, w_k>
             for (int j = 0; j < k; ++j) Wc[j] = W[j];
             int nd = k;
-            if (!split) Wc[nd++] = r;
+            if (!split) Wc[nd++] = rk;
             if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), W[k], 0, st));
             if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, r, W[k], 2 * k, st));
             QXD_TRY(blas_fetch(ctx, 2 * (k + 1), st));
@@ -289,7 +295,8 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             if (!(ww[k] > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
             are[k] = wr_re / ww[k];
             aim[k] = wr_im / ww[k];
-            QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
+            if (rz) QXD_TRY(blas_axpy3(ctx, Pb, n, -are[k], -aim[k], W[k], Z[k], k + 1 < nkv ? Z[k + 1] : r, st));
+            else QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
             rr -= (wr_re * wr_re + wr_im * wr_im) / ww[k];
             *iters += 1;
             K = k + 1;
