@@ -223,12 +223,14 @@ __global__ void __launch_bounds__(kRedThreads) k_norm2(size_t nch, const void* _
     block_reduce_finish<2>(v, o);
 }
 
-// <W_j, v> for j < K
+// <W_j, v> for j < K.  With few vectors each thread takes U chunks per pass, so
+// that about four loads are in flight per thread whatever K is.
 template <int P, int K>
 __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr W, const void* __restrict__ v,
                                                            RedOut o) {
     using R = typename Chunk<P>::R;
     constexpr int NC = Chunk<P>::NC;
+    constexpr int U = (K + 1 >= 4) ? 1 : ((K + 1 >= 2) ? 2 : 4);
     double acc[2 * K];
     R f[2 * K];
 #pragma unroll
@@ -238,20 +240,29 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_dot(size_t nch, MultiPtr 
     }
     int cnt = 0;
     const size_t S = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += S) {
-        cplx<R> y[NC];
-        Chunk<P>::ld(v, i, y);
-        cplx<R> x[K][NC];
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < nch; i0 += S * U) {
+        cplx<R> y[U][NC];
+        cplx<R> x[U][K][NC];
 #pragma unroll
-        for (int j = 0; j < K; ++j) Chunk<P>::ld(W.p[j], i, x[j]);
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * S < nch) {
+                Chunk<P>::ld(v, i0 + u * S, y[u]);
 #pragma unroll
-        for (int j = 0; j < K; ++j)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                f[2 * j] = fma(x[j][c].re, y[c].re, fma(x[j][c].im, y[c].im, f[2 * j]));
-                f[2 * j + 1] = fma(x[j][c].re, y[c].im, fma(-x[j][c].im, y[c].re, f[2 * j + 1]));
+                for (int j = 0; j < K; ++j) Chunk<P>::ld(W.p[j], i0 + u * S, x[u][j]);
             }
-        if (++cnt == kFlush) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (i0 + u * S < nch) {
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        f[2 * j] = fma(x[u][j][c].re, y[u][c].re, fma(x[u][j][c].im, y[u][c].im, f[2 * j]));
+                        f[2 * j + 1] = fma(x[u][j][c].re, y[u][c].im, fma(-x[u][j][c].im, y[u][c].re, f[2 * j + 1]));
+                    }
+            }
+        cnt += U;
+        if (cnt >= kFlush) {
 #pragma unroll
             for (int c = 0; c < 2 * K; ++c) {
                 acc[c] += f[c];
