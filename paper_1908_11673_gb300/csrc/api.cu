@@ -249,10 +249,7 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
                   cudaMalloc(&F.C64[0], 2 * 36 * Vh * sizeof(double2)) == cudaSuccess &&
                   cudaMalloc(&F.C64[1], 2 * 36 * Vh * sizeof(double2)) == cudaSuccess &&
                   cudaMalloc(&F.C32[0], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&F.C32[1], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&F.Vdf, 2 * 36 * Vh * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&F.Cdf[0], 2 * 36 * Vh * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&F.Cdf[1], 2 * 36 * Vh * sizeof(float4)) == cudaSuccess;
+                  cudaMalloc(&F.C32[1], 2 * 18 * Vh * sizeof(float4)) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             free_flavour(F);
@@ -261,7 +258,12 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
     }
     F.f = *f;
     F.set = false;
-    // a deflation subspace belongs to the operator it was built for
+    // double-float copies and a deflation subspace belong to the operator they were built for
+    cudaFree(F.Vdf);
+    cudaFree(F.Cdf[0]);
+    cudaFree(F.Cdf[1]);
+    F.Vdf = nullptr;
+    F.Cdf[0] = F.Cdf[1] = nullptr;
     cudaFree(F.dfl_basis);
     cudaFree(F.dfl_A);
     cudaFree(F.dfl_nbr);

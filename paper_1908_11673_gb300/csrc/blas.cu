@@ -385,6 +385,83 @@ int blas_residual_df64(qxd_ctx* ctx, const void* eta, const void* dx, void* r, s
     return QXD_OK;
 }
 
+// ---- the mixed solver's outer loop in double-float (site by site, FP32 pipe only) ----
+// r = eta - dx (both double-float, one half-lattice field): r32 = r rounded to the
+// FP32 layout, result[slot] = |r|^2 (leading parts, FP32 per site, FP64 sums),
+// result[slot+1] = count of non-finite sites
+__global__ void __launch_bounds__(kRedThreads) k_df_residual(int Vh, const float4* __restrict__ eta,
+                                                             const float4* __restrict__ dx,
+                                                             float4* __restrict__ r32, RedOut o) {
+    double v[2] = {0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<dfl> e[12], d[12];
+        load_spinor<3>(eta, Vh, h, e);
+        load_spinor<3>(dx, Vh, h, d);
+        cplx<float> r[12];
+        float f = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dfl re = df_norm(e[k].re - d[k].re), im = df_norm(e[k].im - d[k].im);
+            r[k] = {re.hi, im.hi};
+            f = fmaf(re.hi, re.hi, fmaf(im.hi, im.hi, f));
+        }
+        if (isfinite(f)) v[0] += f;
+        else v[1] += 1.0;
+        store_spinor<1>(r32, Vh, h, r);
+    }
+    block_reduce_finish<2>(v, o);
+}
+
+// x += e (x double-float, e FP32), one half-lattice field
+__global__ void k_df_add_f32(int Vh, const float4* __restrict__ e32, float4* __restrict__ x) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cplx<float> e[12];
+    load_spinor<1>(e32, Vh, h, e);
+    cplx<dfl> xs[12];
+    load_spinor<3>(x, Vh, h, xs);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) xs[k] = {xs[k].re + dfl(e[k].re, 0.f), xs[k].im + dfl(e[k].im, 0.f)};
+    store_spinor<3>(x, Vh, h, xs);
+}
+
+// r32 = leading parts of a double-float field, one half-lattice field
+__global__ void k_df_to_f32(int Vh, const float4* __restrict__ x, float4* __restrict__ r32) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cplx<dfl> xs[12];
+    load_spinor<3>(x, Vh, h, xs);
+    cplx<float> r[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) r[k] = {df_norm(xs[k].re).hi, df_norm(xs[k].im).hi};
+    store_spinor<1>(r32, Vh, h, r);
+}
+
+int blas_df_residual(qxd_ctx* ctx, const void* eta, const void* dx, void* r32, int slot, cudaStream_t st) {
+    const int Vh = ctx->g.Vh;
+    ProfScope prof(ctx, "df_residual", (double)Vh * (192 + 192 + 96), st);
+    const RedOut o = red_out(ctx, slot);
+    k_df_residual<<<wave_blocks(ctx, k_df_residual, kRedThreads, (size_t)kRedThreads, (size_t)Vh), kRedThreads, 0,
+                    st>>>(Vh, static_cast<const float4*>(eta), static_cast<const float4*>(dx),
+                          static_cast<float4*>(r32), o);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+int blas_df_add_f32(qxd_ctx* ctx, const void* e32, void* x, cudaStream_t st) {
+    const int Vh = ctx->g.Vh;
+    ProfScope prof(ctx, "df_add_f32", (double)Vh * (96 + 192 + 192), st);
+    k_df_add_f32<<<nblocks(Vh, 128), 128, 0, st>>>(Vh, static_cast<const float4*>(e32), static_cast<float4*>(x));
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+int blas_df_to_f32(qxd_ctx* ctx, const void* x, void* r32, cudaStream_t st) {
+    const int Vh = ctx->g.Vh;
+    ProfScope prof(ctx, "df_to_f32", (double)Vh * (192 + 96), st);
+    k_df_to_f32<<<nblocks(Vh, 128), 128, 0, st>>>(Vh, static_cast<const float4*>(x), static_cast<float4*>(r32));
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
 // sum of a real FP64 array over its finite entries, and the count of the others
 __global__ void __launch_bounds__(kRedThreads) k_sum_real(size_t n, const double* __restrict__ a, RedOut o) {
     double v[2] = {0.0, 0.0};

@@ -34,6 +34,12 @@ int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStrea
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
 int blas_residual_df64(qxd_ctx* ctx, const void* eta, const void* dx, void* r, size_t n, cudaStream_t st);
+// The mixed solver's outer loop on double-float half-lattice fields (FP32 pipe only):
+// r32 = FP32(eta - dx) with result[slot] = |r|^2, result[slot+1] = non-finite sites;
+// x += e32; r32 = FP32(x)
+int blas_df_residual(qxd_ctx* ctx, const void* eta, const void* dx, void* r32, int slot, cudaStream_t st);
+int blas_df_add_f32(qxd_ctx* ctx, const void* e32, void* x, cudaStream_t st);
+int blas_df_to_f32(qxd_ctx* ctx, const void* x, void* r32, cudaStream_t st);
 // result[slot] = sum of the finite entries of the real FP64 array a[n], result[slot+1] = count of the others
 int blas_sum_real(qxd_ctx* ctx, const double* a, size_t n, int slot, cudaStream_t st);
 // result[slot + 2j], [slot + 2j + 1] = <W_j, v>, j < k

@@ -353,14 +353,32 @@ int launch_set_flavour(qxd_ctx* ctx, int fl, cudaStream_t st) {
                                   F.C32[0], F.C64[1], F.C32[1], ctx->dev_flag);
     }
     QXD_CUDA(ctx, cudaGetLastError());
-    // double-float copies of the FP64 links and site-diagonal terms (outer residual)
-    QXD_TRY(blas_split_df64(ctx, F.V64, F.Vdf, 2ull * 36 * g.Vh, st));
-    QXD_TRY(blas_split_df64(ctx, F.C64[0], F.Cdf[0], 2ull * 36 * g.Vh, st));
-    QXD_TRY(blas_split_df64(ctx, F.C64[1], F.Cdf[1], 2ull * 36 * g.Vh, st));
     int flag = 0;
     QXD_CUDA(ctx, cudaMemcpyAsync(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));
     if (flag) return qxd_fail(ctx, QXD_ENAN, "set_clover: singular site-diagonal block");
+    return QXD_OK;
+}
+
+// Double-float copies of the FP64 links and of the site-diagonal term (not its
+// inverse), built on the first double-float operator application of the flavour:
+// together they are as large as the FP64 originals, so they exist only where the
+// mixed solver or QXD_DF64 is used.
+int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st) {
+    QxdFlavour& F = ctx->fl[fl];
+    if (F.Vdf) return QXD_OK;
+    const size_t n = 2ull * 36 * ctx->g.Vh;
+    if (cudaMalloc(&F.Vdf, n * sizeof(float4)) != cudaSuccess ||
+        cudaMalloc(&F.Cdf[0], n * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(F.Vdf);
+        cudaFree(F.Cdf[0]);
+        F.Vdf = nullptr;
+        F.Cdf[0] = nullptr;
+        return qxd_fail(ctx, QXD_ENOMEM, "double-float copies of the links and site-diagonal term: allocation failed");
+    }
+    QXD_TRY(blas_split_df64(ctx, F.V64, F.Vdf, n, st));
+    QXD_TRY(blas_split_df64(ctx, F.C64[0], F.Cdf[0], n, st));
     return QXD_OK;
 }
 

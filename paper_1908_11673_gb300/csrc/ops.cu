@@ -12,6 +12,7 @@ size_t half_bytes(const qxd_ctx* ctx, int P) {
 }
 
 int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStream_t st, int nrhs) {
+    if (P == QXD_DF64) QXD_TRY(ensure_df64(ctx, fl, st));
     HopArgs a{};
     a.c_hop = 1.0;
     a.self_mode = 1;

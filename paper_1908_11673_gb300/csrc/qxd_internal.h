@@ -20,8 +20,8 @@ struct QxdFlavour {
     float4* Z32 = nullptr;     // [p][2][Vh]    z^qhat (boundary phase folded in)
     double2* C64[2] = {nullptr, nullptr};  // [p][36][Vh]  diag term, inverse
     float4* C32[2] = {nullptr, nullptr};   // [p][18][Vh]
-    float4* Vdf = nullptr;                 // [p][36][Vh]  V64 as double-float pairs
-    float4* Cdf[2] = {nullptr, nullptr};   // [p][36][Vh]  C64 as double-float pairs
+    float4* Vdf = nullptr;                 // [p][36][Vh]  V64 as double-float pairs (on first use)
+    float4* Cdf[2] = {nullptr, nullptr};   // [p][36][Vh]  C64[0] as double-float pairs (on first use; [1] unused)
     // learned preconditioner
     void* W = nullptr;         // device weights (complex float [layers][cout][cin][9][4][4])
     int nlayers = 0, nch = 0;

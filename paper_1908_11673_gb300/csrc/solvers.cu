@@ -30,30 +30,14 @@ static int status_of_norm(qxd_ctx* ctx, double nonfinite, const char* where) {
 }
 
 // ---------------------------------------------------------------------------
-// r = eta - D x (FP64 data, full lattice); returns |r|^2 in *rr.  df: D x in
-// double-float arithmetic on the FP32 pipe (about 48-bit significands; the
-// FP64 pipe of this GPU runs at 1/64 of the FP32 rate), else in FP64.
+// r = eta - D x (FP64, full lattice); returns |r|^2 in *rr
 int full_residual64(qxd_ctx* ctx, int fl, const Full& eta, const Full& x, const Full& r, const Full& tmp_o,
-                    double* rr, cudaStream_t st, bool df) {
+                    double* rr, cudaStream_t st) {
     const size_t n = 12ull * ctx->g.Vh;
-    if (df) {
-        const size_t hb = half_bytes(ctx, QXD_FP64);
-        void *xe, *xo, *de, *dO;
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 124, hb, &xe));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 125, hb, &xo));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 126, hb, &de));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 127, hb, &dO));
-        QXD_TRY(blas_split_df64(ctx, x.e, xe, n, st));
-        QXD_TRY(blas_split_df64(ctx, x.o, xo, n, st));
-        QXD_TRY(op_Dw(ctx, fl, QXD_DF64, Full{xe, xo}, Full{de, dO}, st));
-        QXD_TRY(blas_residual_df64(ctx, eta.e, de, r.e, n, st));
-        QXD_TRY(blas_residual_df64(ctx, eta.o, dO, r.o, n, st));
-    } else {
-        // r = D x, then r = eta - r
-        QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, r, st));
-        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.e, -1.0, 0.0, r.e, st));
-        QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.o, -1.0, 0.0, r.o, st));
-    }
+    // r = D x, then r = eta - r
+    QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, r, st));
+    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.e, -1.0, 0.0, r.e, st));
+    QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, eta.o, -1.0, 0.0, r.o, st));
     QXD_TRY(blas_norm2(ctx, 0, n, r.e, 0, st));
     QXD_TRY(blas_norm2(ctx, 0, n, r.o, 2, st));
     QXD_TRY(blas_fetch(ctx, 4, st));
@@ -145,7 +129,7 @@ int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, con
         QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.e, 1.0, 0.0, x.e, st));
         QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, dx.o, 1.0, 0.0, x.o, st));
         double rr;
-        QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{to, to}, &rr, st, false));
+        QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{to, to}, &rr, st));
         info->op_applies += 1;
         info->true_relres = std::sqrt(rr) / enorm;
         if (info->true_relres <= s->tol) return QXD_OK;
@@ -353,6 +337,12 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     const size_t n = 12ull * ctx->g.Vh;
     const int P = s->inner;
     const int Pv = vec_prec(P);  // precision of the inner solve's vectors (FP32 for BF16 storage)
+    // Mixed inner precision: the outer loop holds eta, x and D x as double-float
+    // fields (FP64 data, FP32-pipe arithmetic, about 48-bit significands), so the
+    // residual, its FP32 rounding for the inner solve and its norm come from one
+    // pass, and the solution update needs no FP64 arithmetic.  FP64 inner solves
+    // keep the outer loop in FP64.
+    const bool df = P != QXD_FP64;
     const size_t hb64 = half_bytes(ctx, QXD_FP64);
     const size_t hbP = half_bytes(ctx, Pv);
     void *re, *ro, *t64, *bP, *roP, *tP, *eeP, *eoP, *to2;
@@ -366,6 +356,15 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 17, hbP, &eoP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 18, hbP, &to2));
     Full r{re, ro};
+    void *xde = nullptr, *xdo = nullptr, *ede = nullptr, *edo = nullptr, *dxe = nullptr, *dxo = nullptr;
+    if (df) {
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 30, hb64, &xde));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 31, hb64, &xdo));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 32, hb64, &ede));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 33, hb64, &edo));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 34, hb64, &dxe));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 35, hb64, &dxo));
+    }
     QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
     QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
     QXD_TRY(blas_fetch(ctx, 4, st));
@@ -381,26 +380,60 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         info->true_relres = 0.0;
         return QXD_OK;
     }
-    QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb64, cudaMemcpyDeviceToDevice, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb64, cudaMemcpyDeviceToDevice, st));
+    if (df) {
+        QXD_TRY(blas_split_df64(ctx, eta.e, ede, n, st));
+        QXD_TRY(blas_split_df64(ctx, eta.o, edo, n, st));
+        QXD_CUDA(ctx, cudaMemsetAsync(xde, 0, hb64, st));
+        QXD_CUDA(ctx, cudaMemsetAsync(xdo, 0, hb64, st));
+        QXD_TRY(blas_df_to_f32(ctx, ede, tP, st));
+        QXD_TRY(blas_df_to_f32(ctx, edo, roP, st));
+    } else {
+        QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb64, cudaMemcpyDeviceToDevice, st));
+        QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb64, cudaMemcpyDeviceToDevice, st));
+    }
+    // true residual of the current x: relative norm; in the double-float loop it
+    // also leaves FP32(eta - D x) in tP, roP for the next inner solve
+    auto residual = [&](double* rel) -> int {
+        double rr;
+        if (df) {
+            QXD_TRY(op_Dw(ctx, fl, QXD_DF64, Full{xde, xdo}, Full{dxe, dxo}, st));
+            QXD_TRY(blas_df_residual(ctx, ede, dxe, tP, 0, st));
+            QXD_TRY(blas_df_residual(ctx, edo, dxo, roP, 2, st));
+            QXD_TRY(blas_fetch(ctx, 4, st));
+            QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "residual"));
+            rr = ctx->red_host[0] + ctx->red_host[2];
+        } else {
+            QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st));
+        }
+        *rel = std::sqrt(rr) / enorm;
+        return QXD_OK;
+    };
+    // the double-float solution goes to the caller's FP64 field
+    auto finish = [&]() -> int {
+        if (df) {
+            QXD_TRY(blas_join_df64(ctx, xde, x.e, n, st));
+            QXD_TRY(blas_join_df64(ctx, xdo, x.o, n, st));
+        }
+        return QXD_OK;
+    };
     double relres = 1.0;
     bool use_cgnr = false;
     const double itol = s->inner_tol > 0 ? s->inner_tol : (P == QXD_BF16 ? 5e-3 : (P == QXD_FP32 ? 1e-5 : 1e-10));
     for (int outer = 0; outer < 64; ++outer) {
         if (outer > 0) {
-            double rr;
-            QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st, P != QXD_FP64));
+            QXD_TRY(residual(&relres));
             info->op_applies += 1;
-            relres = std::sqrt(rr) / enorm;
             info->true_relres = relres;
             if (verbose()) std::fprintf(stderr, "[qxd dc] outer %d true relres %.6e\n", outer, relres);
-            if (relres <= s->tol) return QXD_OK;
+            if (relres <= s->tol) return finish();
             info->restarts += 1;
         }
         if (info->iters >= s->nmx) break;
         // even-odd source in precision P: b = r_e - H_eo A_oo^-1 r_o
-        QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.e, 0.0, 0.0, tP, st));
-        QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.o, 0.0, 0.0, roP, st));
+        if (!df) {
+            QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.e, 0.0, 0.0, tP, st));
+            QXD_TRY(blas_axpby(ctx, 0, Pv, n, 1.0, 0.0, r.o, 0.0, 0.0, roP, st));
+        }
         QXD_TRY(op_eo_source(ctx, fl, Pv, Full{tP, roP}, bP, to2, st));
         int it = 0;
         const double rtol = std::max(itol, 0.5 * s->tol / relres);
@@ -425,12 +458,17 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         }
         // e_o = A_oo^-1 (r_o - H_oe e_e);  x += e
         QXD_TRY(op_odd_reconstruct(ctx, fl, Pv, roP, eeP, eoP, st));
-        QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
-        QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        if (df) {
+            QXD_TRY(blas_df_add_f32(ctx, eeP, xde, st));
+            QXD_TRY(blas_df_add_f32(ctx, eoP, xdo, st));
+        } else {
+            QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eeP, 1.0, 0.0, x.e, st));
+            QXD_TRY(blas_axpby(ctx, Pv, 0, n, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        }
     }
-    double rr;
-    QXD_TRY(full_residual64(ctx, fl, eta, x, r, Full{t64, t64}, &rr, st, P != QXD_FP64));
-    info->true_relres = std::sqrt(rr) / enorm;
+    QXD_TRY(residual(&relres));
+    info->true_relres = relres;
+    QXD_TRY(finish());
     if (info->true_relres <= s->tol) return QXD_OK;
     return qxd_fail(ctx, QXD_ENOCONV, "FGCR: tolerance not reached within nmx");
 }
