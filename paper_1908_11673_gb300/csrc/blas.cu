@@ -355,16 +355,6 @@ __global__ void k_join_df64(const float4* in, double2* out, size_t n) {
         out[i] = make_double2(to_double(dfl(v.x, v.y)), to_double(dfl(v.z, v.w)));
     }
 }
-// r = eta - dx (dx in double-float)
-__global__ void k_residual_df64(const double2* __restrict__ eta, const float4* __restrict__ dx, double2* __restrict__ r,
-                                size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 e = eta[i];
-        const float4 v = dx[i];
-        r[i] = make_double2(e.x - to_double(dfl(v.x, v.y)), e.y - to_double(dfl(v.z, v.w)));
-    }
-}
-
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st) {
     ProfScope prof(ctx, "split_df64", (double)n * 32, st);
     k_split_df64<<<upd_blocks(ctx, n), 256, 0, st>>>(static_cast<const double2*>(in), static_cast<float4*>(out), n);
@@ -374,13 +364,6 @@ int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStrea
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st) {
     ProfScope prof(ctx, "join_df64", (double)n * 32, st);
     k_join_df64<<<upd_blocks(ctx, n), 256, 0, st>>>(static_cast<const float4*>(in), static_cast<double2*>(out), n);
-    QXD_CUDA(ctx, cudaGetLastError());
-    return QXD_OK;
-}
-int blas_residual_df64(qxd_ctx* ctx, const void* eta, const void* dx, void* r, size_t n, cudaStream_t st) {
-    ProfScope prof(ctx, "residual_df64", (double)n * 48, st);
-    k_residual_df64<<<upd_blocks(ctx, n), 256, 0, st>>>(static_cast<const double2*>(eta), static_cast<const float4*>(dx),
-                                                         static_cast<double2*>(r), n);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }

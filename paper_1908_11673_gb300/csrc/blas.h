@@ -30,10 +30,9 @@ int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* 
 // result[slot] = |a|^2 over finite entries, result[slot+1] = number of non-finite entries
 int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStream_t st);
 // Double-float conversions over n complex numbers (16-byte chunks): FP64 -> double-float
-// (in == out allowed), double-float -> FP64 (in == out allowed), r = eta - dx (dx double-float)
+// and double-float -> FP64 (in == out allowed for both)
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
-int blas_residual_df64(qxd_ctx* ctx, const void* eta, const void* dx, void* r, size_t n, cudaStream_t st);
 // The mixed solver's outer loop on double-float half-lattice fields (FP32 pipe only):
 // r32 = FP32(eta - dx) with result[slot] = |r|^2, result[slot+1] = non-finite sites;
 // x += e32; r32 = FP32(x)
