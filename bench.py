@@ -328,7 +328,8 @@ def run_native(args, w, name):
     if not args.no_fp64_baseline:
         ms64, inf64 = timed(lambda: ctx.solve(0, eta_d, psi_d, kind=qxd.CGNE, tol=1e-10, nmx=200000,
                                               stream=stream), 1)
-        base = {"fp64_cgne_ms": ms64, "iters": inf64[0].iters, "true_relres": inf64[0].true_relres}
+        base = {"fp64_cgne_ms": ms64, "fp64_cgne_iters": inf64[0].iters,
+                "fp64_cgne_true_relres": inf64[0].true_relres}
 
     # ---- next rows of the method on the same system (not part of the timed step) --------
     nxt = None
