@@ -207,6 +207,27 @@ def make_inputs(w, device):
 
 
 # ----------------------------------------------------------------------------------
+# whole-job aggregation over ranks (replicas: each rank solves its own system)
+def max_over_ranks(dist, value, device):
+    """The largest per-rank value (the job's time); `dist` None means one process."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, device):
+    """The sum of the per-rank values (the job's work)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def run_reference(args, w, name):
     """The oracle on the host cores: each step a bounded sample of sites."""
     rank = int(os.environ.get("RANK", "0"))
@@ -285,11 +306,7 @@ def run_native(args, w, name):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
         return ms, infos
 
     # ---- timed region: K mixed-precision solves, kernels timed by event pairs -----
@@ -305,7 +322,6 @@ def run_native(args, w, name):
     flops = hop_launches * (V // 2) * FLOP_PER_SITE
     launches = sum(p["launches"] for p in prof)
     total_ms_k = sum(p["ms"] for p in prof)
-    value_rank = flops / (ms * 1e-3) / 1e9
 
     # the mixed solver's outer residual runs in double-float: check the last timed
     # solution with the FP64 operator before any other solve overwrites it
@@ -377,11 +393,7 @@ def run_native(args, w, name):
         nxt["sdet"] = {"ms": ms_sd / 3, "logdet_per_odd_site": ctx.sdet(0, stream=stream)[0] / (V // 2)}
 
     # ---- aggregate over ranks ----------------------------------------------------------
-    total_value = value_rank
-    if dist:
-        t = torch.tensor([flops], device=dev, dtype=torch.float64)
-        dist.all_reduce(t)
-        total_value = float(t.item()) / (ms * 1e-3) / 1e9
+    total_value = sum_over_ranks(dist, flops, dev) / (ms * 1e-3) / 1e9
     if rank != 0:
         ctx.close()
         dist.destroy_process_group()
