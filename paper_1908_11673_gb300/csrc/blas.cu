@@ -395,6 +395,49 @@ __global__ void __launch_bounds__(kRedThreads) k_df_residual(int Vh, const float
     block_reduce_finish<2>(v, o);
 }
 
+// r32 = FP32(b - y - sigma x) for double-float b, y = Q2 x and x (one half-lattice
+// field); result[slot] = |r|^2, result[slot+1] = count of non-finite sites
+__global__ void __launch_bounds__(kRedThreads) k_df_shift_residual(int Vh, const float4* __restrict__ b,
+                                                                   const float4* __restrict__ y,
+                                                                   const float4* __restrict__ x, float sig_hi,
+                                                                   float sig_lo, float4* __restrict__ r32, RedOut o) {
+    double v[2] = {0.0, 0.0};
+    const dfl sig(sig_hi, sig_lo);
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        cplx<dfl> bs[12], ys[12], xs[12];
+        load_spinor<3>(b, Vh, h, bs);
+        load_spinor<3>(y, Vh, h, ys);
+        load_spinor<3>(x, Vh, h, xs);
+        cplx<float> r[12];
+        float f = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dfl re = df_norm(bs[k].re - (ys[k].re + sig * xs[k].re));
+            const dfl im = df_norm(bs[k].im - (ys[k].im + sig * xs[k].im));
+            r[k] = {re.hi, im.hi};
+            f = fmaf(re.hi, re.hi, fmaf(im.hi, im.hi, f));
+        }
+        if (isfinite(f)) v[0] += f;
+        else v[1] += 1.0;
+        store_spinor<1>(r32, Vh, h, r);
+    }
+    block_reduce_finish<2>(v, o);
+}
+
+int blas_df_shift_residual(qxd_ctx* ctx, const void* b, const void* y, const void* x, double sigma, void* r32,
+                           int slot, cudaStream_t st) {
+    const int Vh = ctx->g.Vh;
+    ProfScope prof(ctx, "df_shift_residual", (double)Vh * (3 * 192 + 96), st);
+    const RedOut o = red_out(ctx, slot);
+    const dfl sg(sigma);
+    k_df_shift_residual<<<wave_blocks(ctx, k_df_shift_residual, kRedThreads, (size_t)kRedThreads, (size_t)Vh),
+                          kRedThreads, 0, st>>>(Vh, static_cast<const float4*>(b), static_cast<const float4*>(y),
+                                                static_cast<const float4*>(x), sg.hi, sg.lo,
+                                                static_cast<float4*>(r32), o);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
 // x += e (x double-float, e FP32), one half-lattice field
 __global__ void k_df_add_f32(int Vh, const float4* __restrict__ e32, float4* __restrict__ x) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;

@@ -39,6 +39,9 @@ int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream
 int blas_df_residual(qxd_ctx* ctx, const void* eta, const void* dx, void* r32, int slot, cudaStream_t st);
 int blas_df_add_f32(qxd_ctx* ctx, const void* e32, void* x, cudaStream_t st);
 int blas_df_to_f32(qxd_ctx* ctx, const void* x, void* r32, cudaStream_t st);
+// r32 = FP32(b - y - sigma x), b, y, x double-float; result[slot] = |r|^2, [slot+1] = non-finite sites
+int blas_df_shift_residual(qxd_ctx* ctx, const void* b, const void* y, const void* x, double sigma, void* r32,
+                           int slot, cudaStream_t st);
 // result[slot] = sum of the finite entries of the real FP64 array a[n], result[slot+1] = count of the others
 int blas_sum_real(qxd_ctx* ctx, const double* a, size_t n, int slot, cudaStream_t st);
 // result[slot + 2j], [slot + 2j + 1] = <W_j, v>, j < k

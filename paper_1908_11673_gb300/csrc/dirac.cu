@@ -128,10 +128,11 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
         d.diag = F.C64[0] + (size_t)po * 36 * Vh;
         d.diaginv = F.C64[1] + (size_t)po * 36 * Vh;
     } else if (prec == QXD_DF64) {
-        // double-float keeps the site-diagonal term only (D itself, no inverse)
-        if (a.post_mode != 0 || !F.Vdf) return qxd_fail(ctx, QXD_EARG, "double-float hop: D only");
+        // the copies are built by ensure_df64 (the inverse only for operators that need it)
+        if (!F.Vdf || !F.Cdf[0] || (a.post_mode == 1 && !F.Cdf[1]))
+            return qxd_fail(ctx, QXD_ESTATE, "double-float hop: copies of the flavour not built");
         d.diag = F.Cdf[0] + (size_t)po * 36 * Vh;
-        d.diaginv = nullptr;
+        d.diaginv = F.Cdf[1] ? F.Cdf[1] + (size_t)po * 36 * Vh : nullptr;
     } else {
         d.diag = F.C32[0] + (size_t)po * 18 * Vh;
         d.diaginv = F.C32[1] + (size_t)po * 18 * Vh;

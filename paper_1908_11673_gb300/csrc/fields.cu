@@ -360,25 +360,25 @@ int launch_set_flavour(qxd_ctx* ctx, int fl, cudaStream_t st) {
     return QXD_OK;
 }
 
-// Double-float copies of the FP64 links and of the site-diagonal term (not its
-// inverse), built on the first double-float operator application of the flavour:
-// together they are as large as the FP64 originals, so they exist only where the
-// mixed solver or QXD_DF64 is used.
-int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st) {
+// Double-float copies of the FP64 links and of the site-diagonal term (and, when
+// an operator needs it, of its inverse), built on the first double-float
+// application of the flavour: each is as large as its FP64 original, so they
+// exist only where the mixed solvers or QXD_DF64 are used.
+int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st, bool inverse) {
     QxdFlavour& F = ctx->fl[fl];
-    if (F.Vdf) return QXD_OK;
     const size_t n = 2ull * 36 * ctx->g.Vh;
-    if (cudaMalloc(&F.Vdf, n * sizeof(float4)) != cudaSuccess ||
-        cudaMalloc(&F.Cdf[0], n * sizeof(float4)) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(F.Vdf);
-        cudaFree(F.Cdf[0]);
-        F.Vdf = nullptr;
-        F.Cdf[0] = nullptr;
-        return qxd_fail(ctx, QXD_ENOMEM, "double-float copies of the links and site-diagonal term: allocation failed");
-    }
-    QXD_TRY(blas_split_df64(ctx, F.V64, F.Vdf, n, st));
-    QXD_TRY(blas_split_df64(ctx, F.C64[0], F.Cdf[0], n, st));
+    auto build = [&](float4** dst, const double2* src) -> int {
+        if (*dst) return QXD_OK;
+        if (cudaMalloc(dst, n * sizeof(float4)) != cudaSuccess) {
+            cudaGetLastError();
+            *dst = nullptr;
+            return qxd_fail(ctx, QXD_ENOMEM, "double-float copy of the links or site-diagonal terms: allocation failed");
+        }
+        return blas_split_df64(ctx, src, *dst, n, st);
+    };
+    QXD_TRY(build(&F.Vdf, F.V64));
+    QXD_TRY(build(&F.Cdf[0], F.C64[0]));
+    if (inverse) QXD_TRY(build(&F.Cdf[1], F.C64[1]));
     return QXD_OK;
 }
 

@@ -32,6 +32,7 @@ int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStre
 
 int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out_e, void* tmp_o, cudaStream_t st,
             int nrhs) {
+    if (P == QXD_DF64) QXD_TRY(ensure_df64(ctx, fl, st, true));
     HopArgs a{};
     a.nrhs = nrhs;
     // tmp_o = A_oo^-1 H_oe (gamma5) in_e

@@ -14,9 +14,9 @@ struct Full {
 // bytes of one half-lattice field in precision P (0 FP64, 1 FP32, 2 BF16)
 size_t half_bytes(const qxd_ctx* ctx, int P);
 
-// double-float copies of the flavour's FP64 links and site-diagonal term (fields.cu),
-// built on first use
-int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st);
+// double-float copies of the flavour's FP64 links and site-diagonal term, and with
+// inverse = true of the inverse term too (fields.cu), built on first use
+int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st, bool inverse = false);
 // out = D in (eq. dirac):  out_e = A_ee in_e + H_eo in_o,  out_o = A_oo in_o + H_oe in_e
 int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStream_t st, int nrhs = 1);
 // out_e = Dhat in_e = A_ee in_e - H_eo A_oo^-1 H_oe in_e (dagger: gamma5 Dhat gamma5); tmp_o: odd scratch

@@ -845,13 +845,32 @@ int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solv
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 106, hb64, &to));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 120, half_bytes(ctx, QXD_FP32), &eP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 121, half_bytes(ctx, QXD_FP32), &rP));
+    // With an FP32 Krylov space the residuals b - (Q2 + s_j) x_j are taken on the FP64
+    // data in double-float arithmetic (FP32 pipe); they land in FP32 directly for the
+    // correction solve.  A plain FP64 run keeps FP64.
+    const bool df = P != QXD_FP64;
+    void *bdf = nullptr, *xdf = nullptr, *ydf = nullptr, *tdf = nullptr;
+    if (df) {
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 36, hb64, &bdf));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 37, hb64, &xdf));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 38, hb64, &ydf));
+        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 39, hb64, &tdf));
+        QXD_TRY(blas_split_df64(ctx, b64, bdf, n, st));
+    }
     double worst = 0.0;
     for (int j = 0; j < ns; ++j) {
         char* xj = X64 + j * hb64;
         for (int pass = 0; pass < 16; ++pass) {
-            QXD_TRY(op_normal(ctx, fl, 0, sigma[j], xj, r64, te, to, st));
-            QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, b64, -1.0, 0.0, r64, st));
-            QXD_TRY(blas_norm2(ctx, 0, n, r64, 0, st));
+            if (df) {
+                QXD_TRY(blas_split_df64(ctx, xj, xdf, n, st));
+                QXD_TRY(op_Dhat(ctx, fl, QXD_DF64, 0, xdf, tdf, to, st));
+                QXD_TRY(op_Dhat(ctx, fl, QXD_DF64, 1, tdf, ydf, to, st));
+                QXD_TRY(blas_df_shift_residual(ctx, bdf, ydf, xdf, sigma[j], rP, 0, st));
+            } else {
+                QXD_TRY(op_normal(ctx, fl, 0, sigma[j], xj, r64, te, to, st));
+                QXD_TRY(blas_axpby(ctx, 0, 0, n, 1.0, 0.0, b64, -1.0, 0.0, r64, st));
+                QXD_TRY(blas_norm2(ctx, 0, n, r64, 0, st));
+            }
             QXD_TRY(blas_fetch(ctx, 2, st));
             QXD_TRY(status_of_norm(ctx, ctx->red_host[1], "MSCG residual"));
             const double rel = std::sqrt(ctx->red_host[0]) / bn;
@@ -861,7 +880,7 @@ int solve_mscg(qxd_ctx* ctx, int fl, int ns, const double* sigma, const qxd_solv
                 break;
             }
             info->restarts += 1;
-            QXD_TRY(blas_axpby(ctx, 0, 1, n, 1.0, 0.0, r64, 0.0, 0.0, rP, st));
+            if (!df) QXD_TRY(blas_axpby(ctx, 0, 1, n, 1.0, 0.0, r64, 0.0, 0.0, rP, st));
             int ci = 0;
             QXD_TRY(cg_shifted(ctx, fl, 1, sigma[j], rP, eP, s->nmx - info->iters, std::max(1e-5, 0.5 * s->tol / rel),
                                &ci, st));
