@@ -381,6 +381,21 @@ int qxd_profile(qxd_ctx* ctx, int mode);
  * counted once per launch: the roofline numerator).  QXD_EARG past the last class. */
 int qxd_profile_entry(qxd_ctx* ctx, int i, char* name, int len, long long* launches, double* ms, double* bytes);
 
+/* ---- host-only helpers (no device, no context) ----
+ * The partial-fraction residues the rational functions above use:
+ * sigma[j-k] = (nu_j^2 - mu_j^2) prod_{m != j} (nu_m^2 - mu_j^2) / (mu_m^2 - mu_j^2),
+ * j = k..l, of P_{k,l} (App. A.2), and the residues (sigma, sigma_t) of Ptilde_{k,l} - 1 at
+ * q2 = -nu_j^2 and q2 = -mutilde_j^2 (App. A.3, W_rtm).  QXD_EARG for bad arguments or
+ * coinciding poles. */
+int qxd_rat_residues(const qxd_rational* r, int k, int l, double* sigma);
+int qxd_rtm_residues(const qxd_rational* r_mu, const qxd_rational* r_t, int k, int l, double* sigma,
+                     double* sigma_t);
+
+/* The 4^4 block grid of SAP and deflation for geometry g: *nblocks (may be NULL) = Nb,
+ * nbr_out (may be NULL) int [Nb][9] as in qxd_dfl_little.  QXD_EARG for an invalid
+ * geometry or a simulated extent that is not a multiple of 8. */
+int qxd_block_neighbours(const qxd_geom* g, int* nbr_out, int* nblocks);
+
 /* Message describing the last failing call on ctx (never NULL). */
 const char* qxd_last_error(qxd_ctx* ctx);
 

@@ -131,6 +131,26 @@ int check_fl(qxd_ctx* ctx, int fl) {
     return QXD_OK;
 }
 
+bool make_geo(const qxd_geom* g, Geo* G) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (g->L[mu] < 2 || (g->L[mu] & 1)) return false;
+    if (g->cstar < 0 || g->cstar > 3) return false;
+    if (g->cstar > 0 && (g->theta[1] != 0.0 || g->theta[2] != 0.0 || g->theta[3] != 0.0)) return false;
+    long long V = 1;
+    for (int mu = 0; mu < 4; ++mu) V *= g->L[mu];
+    if (g->cstar) V *= 2;
+    if (V / 2 > 0x7fffffffLL / 36) return false;  // 32-bit half-lattice indexing
+    G->N[0] = g->L[0];
+    G->N[1] = g->cstar ? 2 * g->L[1] : g->L[1];
+    G->N[2] = g->L[2];
+    G->N[3] = g->L[3];
+    G->L1 = g->L[1];
+    G->cstar = g->cstar;
+    G->V = V;
+    G->Vh = (int)(V / 2);
+    return true;
+}
+
 static void free_flavour(QxdFlavour& F) {
     cudaFree(F.V64);
     cudaFree(F.Z32);
@@ -152,14 +172,8 @@ extern "C" {
 int qxd_create(const qxd_geom* g, int device, qxd_ctx** out) {
     if (!g || !out) return QXD_EARG;
     *out = nullptr;
-    for (int mu = 0; mu < 4; ++mu)
-        if (g->L[mu] < 2 || (g->L[mu] & 1)) return QXD_EARG;
-    if (g->cstar < 0 || g->cstar > 3) return QXD_EARG;
-    if (g->cstar > 0 && (g->theta[1] != 0.0 || g->theta[2] != 0.0 || g->theta[3] != 0.0)) return QXD_EARG;
-    long long V = 1;
-    for (int mu = 0; mu < 4; ++mu) V *= g->L[mu];
-    if (g->cstar) V *= 2;
-    if (V / 2 > 0x7fffffffLL / 36) return QXD_EARG;  // 32-bit half-lattice indexing
+    Geo G;
+    if (!make_geo(g, &G)) return QXD_EARG;
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return QXD_ECUDA;
@@ -168,15 +182,7 @@ int qxd_create(const qxd_geom* g, int device, qxd_ctx** out) {
     if (!ctx) return QXD_ENOMEM;
     ctx->geom = *g;
     ctx->device = device;
-    Geo& G = ctx->g;
-    G.N[0] = g->L[0];
-    G.N[1] = g->cstar ? 2 * g->L[1] : g->L[1];
-    G.N[2] = g->L[2];
-    G.N[3] = g->L[3];
-    G.L1 = g->L[1];
-    G.cstar = g->cstar;
-    G.V = V;
-    G.Vh = (int)(V / 2);
+    ctx->g = G;
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device);
     const size_t Vh = G.Vh;
     bool ok = cudaMalloc(&ctx->U64, 2 * 36 * Vh * sizeof(double2)) == cudaSuccess &&

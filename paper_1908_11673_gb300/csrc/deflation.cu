@@ -15,6 +15,7 @@
 // A[B][s][l][k] = <phi_k|_B, D phi_l|_{B_s}> (s = 0 the block itself, 1 + 2 mu the
 // block across the +mu face, 2 + 2 mu across the -mu face), so that lane k of a
 // warp reads consecutive entries when it forms row k of A x.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -272,16 +273,17 @@ __global__ void k_dfl_coarse(DflGrid G, int Ns, const int* __restrict__ nbr, con
     y[(size_t)B * Ns + k] = make_float2(acc.re, acc.im);
 }
 
-DflGrid dfl_grid(const qxd_ctx* ctx) {
+DflGrid dfl_grid(const Geo& g) {
     DflGrid G;
     G.Nb = 1;
     for (int mu = 0; mu < 4; ++mu) {
-        G.nb[mu] = ctx->g.N[mu] / kBlk;
+        G.nb[mu] = g.N[mu] / kBlk;
         G.Nb *= G.nb[mu];
     }
-    G.Vh = ctx->g.Vh;
+    G.Vh = g.Vh;
     return G;
 }
+DflGrid dfl_grid(const qxd_ctx* ctx) { return dfl_grid(ctx->g); }
 
 size_t field_chunks(const qxd_ctx* ctx) { return (size_t)12 * ctx->g.Vh; }  // float4 per full FP32 field
 
@@ -322,9 +324,8 @@ int orthonormalise(qxd_ctx* ctx, QxdFlavour& F, cudaStream_t st) {
 }
 
 // block neighbour table [Nb][9] from the lattice neighbour map (C* shifts included)
-void neighbour_table(const qxd_ctx* ctx, std::vector<int>& nbr) {
-    const DflGrid G = dfl_grid(ctx);
-    const Geo& g = ctx->g;
+void neighbour_table(const Geo& g, std::vector<int>& nbr) {
+    const DflGrid G = dfl_grid(g);
     nbr.assign((size_t)G.Nb * 9, 0);
     auto block_of = [&](int lex) {
         int x[4];
@@ -554,7 +555,7 @@ int qxd_dfl_setup(qxd_ctx* ctx, int fl, const qxd_dfl_params* prm, const void* s
     F.dfl_cnmx = prm->cnmx;
     F.dfl_cnkv = prm->cnkv;
     std::vector<int> nbr;
-    neighbour_table(ctx, nbr);
+    neighbour_table(ctx->g, nbr);
     QXD_CUDA(ctx, cudaMemcpyAsync(F.dfl_nbr, nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice, st));
     // seeds: complex64 [Ns][V][4][3] -> internal FP32 fields
     const size_t cb = (size_t)ctx->g.V * 12 * 8;
@@ -658,6 +659,22 @@ int qxd_dfl_apply(qxd_ctx* ctx, int fl, const void* in, void* out, qxd_info* inf
         *info = qxd_info{};
         info->iters = it;
         info->true_relres = rel;
+    }
+    return QXD_OK;
+}
+
+int qxd_block_neighbours(const qxd_geom* geom, int* nbr_out, int* nblocks) {
+    if (!geom) return QXD_EARG;
+    Geo g;
+    if (!make_geo(geom, &g)) return QXD_EARG;
+    for (int mu = 0; mu < 4; ++mu)
+        if (g.N[mu] % (2 * kBlk)) return QXD_EARG;
+    const DflGrid G = dfl_grid(g);
+    if (nblocks) *nblocks = G.Nb;
+    if (nbr_out) {
+        std::vector<int> nbr;
+        neighbour_table(g, nbr);
+        std::copy(nbr.begin(), nbr.end(), nbr_out);
     }
     return QXD_OK;
 }

@@ -115,6 +115,8 @@ int stage_in(qxd_ctx* ctx, int slot, const void* p, size_t bytes, const void** d
 int stage_out(qxd_ctx* ctx, int slot, void* p, size_t bytes, void** dev, bool* host);
 int finish_out(qxd_ctx* ctx, void* p, const void* dev, size_t bytes, bool host, cudaStream_t st);
 int check_fl(qxd_ctx* ctx, int fl);
+// simulated-lattice geometry of a qxd_geom; false if the geometry is invalid
+bool make_geo(const qxd_geom* g, qxd::Geo* G);
 
 // workspace slots
 enum {

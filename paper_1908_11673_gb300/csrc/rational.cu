@@ -18,6 +18,13 @@ namespace qxd {
 
 namespace {
 
+bool rational_ok(const qxd_rational* r) {
+    if (!r || !r->nu || !r->mu || r->n < 1 || r->n > kMaxShifts || !std::isfinite(r->A)) return false;
+    for (int j = 0; j < r->n; ++j)
+        if (!std::isfinite(r->nu[j]) || !std::isfinite(r->mu[j])) return false;
+    return true;
+}
+
 int check_rational(qxd_ctx* ctx, const qxd_rational* r, const char* what) {
     if (!r || !r->nu || !r->mu) return qxd_fail(ctx, QXD_EARG, std::string(what) + ": NULL rational approximation");
     if (r->n < 1 || r->n > kMaxShifts)
@@ -34,26 +41,32 @@ int check_range(qxd_ctx* ctx, const qxd_rational* r, int k, int l, const char* w
     return QXD_OK;
 }
 
-// residues sigma_j (j = k..l) of P_{k,l} - 1 at q2 = -mu_j^2 (App. A.2)
-int factor_residues(qxd_ctx* ctx, const qxd_rational* r, int k, int l, double* sig) {
+// residues sigma_j (j = k..l) of P_{k,l} - 1 at q2 = -mu_j^2 (App. A.2); false if two
+// mu_j^2 of the factor coincide
+bool factor_residues_host(const qxd_rational* r, int k, int l, double* sig) {
     for (int j = k; j <= l; ++j) {
         const double p = -r->mu[j] * r->mu[j];
         double s = r->nu[j] * r->nu[j] + p;
         for (int m = k; m <= l; ++m) {
             if (m == j) continue;
             const double den = r->mu[m] * r->mu[m] + p;
-            if (den == 0.0) return qxd_fail(ctx, QXD_EARG, "rational factor: the mu_j^2 must be distinct");
+            if (den == 0.0) return false;
             s *= (r->nu[m] * r->nu[m] + p) / den;
         }
         sig[j - k] = s;
     }
+    return true;
+}
+int factor_residues(qxd_ctx* ctx, const qxd_rational* r, int k, int l, double* sig) {
+    if (!factor_residues_host(r, k, l, sig))
+        return qxd_fail(ctx, QXD_EARG, "rational factor: the mu_j^2 must be distinct");
     return QXD_OK;
 }
 
 // residues of Ptilde_{k,l} - 1 at q2 = -nu_j^2 (sig) and q2 = -mutilde_j^2 (sigt),
-// Ptilde_{k,l}(q2) = prod_j (q2 + mu_j^2)(q2 + nutilde_j^2) / ((q2 + nu_j^2)(q2 + mutilde_j^2))
-int rtm_residues(qxd_ctx* ctx, const qxd_rational* rm, const qxd_rational* rt, int k, int l, double* sig,
-                 double* sigt) {
+// Ptilde_{k,l}(q2) = prod_j (q2 + mu_j^2)(q2 + nutilde_j^2) / ((q2 + nu_j^2)(q2 + mutilde_j^2));
+// false if two poles coincide
+bool rtm_residues_host(const qxd_rational* rm, const qxd_rational* rt, int k, int l, double* sig, double* sigt) {
     auto sq = [](double v) { return v * v; };
     for (int j = k; j <= l; ++j) {
         for (int which = 0; which < 2; ++which) {
@@ -66,10 +79,16 @@ int rtm_residues(qxd_ctx* ctx, const qxd_rational* rm, const qxd_rational* rt, i
                 s *= (sq(rm->mu[m]) + p) * (sq(rt->nu[m]) + p);
                 d *= (sq(rm->nu[m]) + p) * (sq(rt->mu[m]) + p);
             }
-            if (d == 0.0) return qxd_fail(ctx, QXD_EARG, "rw_rtm: the poles nu_j^2 and mutilde_j^2 must be distinct");
+            if (d == 0.0) return false;
             (which == 0 ? sig : sigt)[j - k] = s / d;
         }
     }
+    return true;
+}
+int rtm_residues(qxd_ctx* ctx, const qxd_rational* rm, const qxd_rational* rt, int k, int l, double* sig,
+                 double* sigt) {
+    if (!rtm_residues_host(rm, rt, k, l, sig, sigt))
+        return qxd_fail(ctx, QXD_EARG, "rw_rtm: the poles nu_j^2 and mutilde_j^2 must be distinct");
     return QXD_OK;
 }
 
@@ -362,6 +381,19 @@ int qxd_sdet(qxd_ctx* ctx, int fl, double* logdet, int* nneg, void* stream) {
     *logdet = ctx->red_host[0];
     if (nneg) *nneg = (int)ctx->red_host[2];
     return QXD_OK;
+}
+
+int qxd_rat_residues(const qxd_rational* r, int k, int l, double* sigma) {
+    if (!rational_ok(r) || !sigma || k < 0 || l < k || l >= r->n) return QXD_EARG;
+    return factor_residues_host(r, k, l, sigma) ? QXD_OK : QXD_EARG;
+}
+
+int qxd_rtm_residues(const qxd_rational* r_mu, const qxd_rational* r_t, int k, int l, double* sigma,
+                     double* sigma_t) {
+    if (!rational_ok(r_mu) || !rational_ok(r_t) || r_mu->n != r_t->n || !sigma || !sigma_t || k < 0 || l < k ||
+        l >= r_mu->n)
+        return QXD_EARG;
+    return rtm_residues_host(r_mu, r_t, k, l, sigma, sigma_t) ? QXD_OK : QXD_EARG;
 }
 
 }  // extern "C"

@@ -28,6 +28,7 @@ EXPORTS = ["qxd_create", "qxd_destroy", "qxd_set_links", "qxd_set_clover", "qxd_
            "qxd_set_sap", "qxd_sap_apply", "qxd_ptc_apply", "qxd_ptc_loss_grad", "qxd_ptc_train", "qxd_ptc_record_pairs",
            "qxd_rat_apply", "qxd_pf_action", "qxd_rw_rat", "qxd_rw_rtm", "qxd_sdet",
            "qxd_dfl_setup", "qxd_dfl_basis", "qxd_dfl_little", "qxd_dfl_apply",
+           "qxd_rat_residues", "qxd_rtm_residues", "qxd_block_neighbours",
            "qxd_profile", "qxd_profile_entry", "qxd_last_error", "qxd_volume"]
 
 
@@ -123,6 +124,9 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_dfl_basis": (i, [vp, i, i, vp, vp]),
         "qxd_dfl_little": (i, [vp, i, vp, vp, ctypes.POINTER(i), vp]),
         "qxd_dfl_apply": (i, [vp, i, vp, vp, ctypes.POINTER(Info), vp]),
+        "qxd_rat_residues": (i, [ctypes.POINTER(Rational), i, i, vp]),
+        "qxd_rtm_residues": (i, [ctypes.POINTER(Rational), ctypes.POINTER(Rational), i, i, vp, vp]),
+        "qxd_block_neighbours": (i, [ctypes.POINTER(Geom), vp, ctypes.POINTER(i)]),
         "qxd_profile": (i, [vp, i]),
         "qxd_profile_entry": (i, [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ctypes.c_longlong),
                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -136,6 +140,40 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
     if path == LIBPATH:
         _lib = lib
     return lib
+
+
+def rat_residues(r, k, l):
+    """Partial-fraction residues sigma_j, j = k..l, of the factor P_{k,l} (host code of the library)."""
+    lib = load_library()
+    out = np.zeros(max(l - k + 1, 1), dtype=np.float64)
+    rc = lib.qxd_rat_residues(ctypes.byref(r), int(k), int(l), out.ctypes.data)
+    if rc:
+        raise QxdError(rc, "rat_residues: bad arguments or coinciding poles")
+    return out
+
+
+def rtm_residues(r_mu, r_t, k, l):
+    """Residues (sigma, sigma_t) of Ptilde_{k,l} - 1 (host code of the library)."""
+    lib = load_library()
+    s1 = np.zeros(max(l - k + 1, 1), dtype=np.float64)
+    s2 = np.zeros(max(l - k + 1, 1), dtype=np.float64)
+    rc = lib.qxd_rtm_residues(ctypes.byref(r_mu), ctypes.byref(r_t), int(k), int(l), s1.ctypes.data, s2.ctypes.data)
+    if rc:
+        raise QxdError(rc, "rtm_residues: bad arguments or coinciding poles")
+    return s1, s2
+
+
+def block_neighbours(L, cstar=0, theta=(np.pi, 0.0, 0.0, 0.0)):
+    """Block neighbour table [Nb][9] of the 4^4 block grid (host code of the library)."""
+    lib = load_library()
+    g = Geom((ctypes.c_int * 4)(*[int(x) for x in L]), int(cstar), (ctypes.c_double * 4)(*[float(t) for t in theta]))
+    nb = ctypes.c_int()
+    rc = lib.qxd_block_neighbours(ctypes.byref(g), None, ctypes.byref(nb))
+    if rc:
+        raise QxdError(rc, "block_neighbours: invalid geometry or extents not multiples of 8")
+    out = np.zeros((nb.value, 9), dtype=np.int32)
+    lib.qxd_block_neighbours(ctypes.byref(g), out.ctypes.data, None)
+    return out
 
 
 def _ptr(a):
