@@ -29,6 +29,9 @@ Readings where the paper is silent (each used identically by every test):
     leaves at x (the construction the paper takes from Luescher et al. 1996),
     without a traceless projection;
   * the SW sums run over all ordered pairs (mu, nu) as printed.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 

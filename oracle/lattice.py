@@ -16,6 +16,9 @@ Neighbours on the extended lattice:
 
 Site index: lexicographic with x0 slowest, idx = ((x0*N1 + x1)*N2 + x2)*N3 + x3
 where N = extended extents.  Parity = (x0 + x1 + x2 + x3) mod 2 (0 = even).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 

@@ -24,6 +24,9 @@ Gradient (Wirtinger): G = dL/dW^* = sum_x delta_c(x) (T_d a_{c'}(x))^+ per
 layer, with delta = (out - e)/|e|^2 at the output and delta' = layer^+ delta
 propagated backwards (layer^+ uses W^+ and T_d^+ = T_{opposite d}).
 The gradient with respect to the real and imaginary parts of W is 2 Re G, 2 Im G.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 

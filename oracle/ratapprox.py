@@ -7,6 +7,9 @@
 
 The coefficients are inputs (the paper prints a degree-10 example in its sample
 input file, App. C); `load` reads them from a text record.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 

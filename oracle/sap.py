@@ -26,6 +26,9 @@ The minimal-residual steps and the colouring are as in Luescher's SAP (which
 the paper uses through openQCD); the block even-odd splitting is the standard
 one.  As a preconditioner of the even-odd operator Dhat the project uses
 (M (r_e, 0))_e, because Dhat^-1 = (D^-1)_ee.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 

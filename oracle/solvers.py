@@ -2,6 +2,9 @@
 equations (CGNE), multi-shift CG (MSCG, for the shifted systems of the rational
 approximation, App. A.2) and flexible restarted GCR.  Plain NumPy, FP64.
 Vectors are complex arrays of any shape; inner products are <a,b> = sum conj(a) b.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
+benchmark's CPU baseline, never by the library.
 """
 from __future__ import annotations
 
