@@ -51,3 +51,22 @@ def test_null_context_is_safe(lib):
     assert lib.qxd_volume(None) == 0
     assert lib.qxd_last_error(None) == b"NULL context"
     lib.qxd_destroy(None)
+
+
+def declared_arities():
+    """Number of parameters of every function prototype in include/qxd.h."""
+    src = open(os.path.join(ROOT, "include", "qxd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(?:int|void|long long|const char\*)\s+\**(qxd_[A-Za-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src,
+                         flags=re.S):
+        params = " ".join(m.group(2).split())
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_header(lib):
+    arity = declared_arities()
+    assert set(arity) == set(qxd.EXPORTS)
+    for name, n in arity.items():
+        assert len(getattr(lib, name).argtypes) == n, name
