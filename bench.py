@@ -25,7 +25,7 @@ Reported:
              setup timed apart) against the unpreconditioned one, and the
              pseudofermion action of the printed degree-10 rational approximation
              (App. A.2: one 10-shift multi-shift CG plus FP64 assembly) and the
-             small-determinant action (Sec. 2.2), each timed with CUDA events.
+             small-determinant action (Sec. 2.3), each timed with CUDA events.
 
 --impl reference times the oracle (the plain CPU implementation) on the same
 metric, each step a bounded sample of sites of the same workload.
@@ -54,7 +54,7 @@ FP64_PEAK_TFLOPS = 1.19
 
 
 # DRAM bytes per output site measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# on the 24^3x48 lattice for the current kernels (profiles/k_hop_mr_traffic_24x24x24x48.md);
+# on the 24^3x48 lattice for the current kernels;
 # a launch on another lattice moves these bytes times its V/2 sites.
 NCU_BYTES_PER_SITE = {"hop_fp32_self1_post0": 1000.6, "hop_fp32_self0_post1": 898.4}
 
@@ -104,7 +104,8 @@ WORKLOADS = {
 }
 
 
-def workload_desc(name, w):
+def workload_desc(name, w, args, world=1):
+    """The `config` object: identical keys on the native and the reference arm."""
     L = w["L"]
     ext = (L[0], 2 * L[1] if w["cstar"] else L[1], L[2], L[3])
     return {
@@ -116,6 +117,8 @@ def workload_desc(name, w):
         "solver": "FGCR on Dhat, inner solve in FP32 (or BF16 basis storage), FP64 defect correction",
         "tol": 1e-10,
         "l2": "working set (links, SW terms, Krylov vectors) >> 129 MB L2; no flush",
+        "nkv": args.nkv, "inner": args.inner,
+        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
     }
 
 
@@ -198,6 +201,64 @@ def oracle_rate(w, U, A, psi, seconds, rng_seed=0):
     return FLOP_PER_SITE * n / dt / 1e9, n, dt
 
 
+def _oracle_worker(job):
+    """One process of the all-core oracle timing: D_w at its share of the sites,
+    fields read from memory-mapped .npy files.  Returns (sites, wall start, wall end)."""
+    import sys as _sys
+    _sys.path.insert(0, job["root"])
+    from oracle import DiracOperator, Flavour, GaugeField, Geometry
+    w = job["w"]
+    U = np.load(job["U"], mmap_mode="r")
+    A = np.load(job["A"], mmap_mode="r")
+    psi = np.load(job["psi"], mmap_mode="r")
+    geom = Geometry(w["L"], w["cstar"], w["theta"])
+    op = DiracOperator(GaugeField(geom, U, A, w["invqel"]), Flavour(w["qhat"], w["kappa"], w["su3csw"], w["u1csw"]))
+    sites = np.asarray(job["sites"], dtype=np.int64)
+    op.apply(psi, sites[:64])  # touch the pages of the code path before the clock starts
+    t0 = time.time()
+    op.apply(psi, sites)
+    return len(sites), t0, time.time()
+
+
+def oracle_rate_all_cores(w, U, A, psi, seconds, single_rate):
+    """The oracle on every core of this process's affinity set: one spawned worker
+    per core (OMP/BLAS threads pinned to 1), each applying D_w at its own share of
+    a random sample of sites sized for about `seconds` of wall time from the
+    single-core rate.  Returns (Gflop/s, cores, sites, wall s)."""
+    import multiprocessing as mp
+    import shutil
+    import tempfile
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    V = psi.shape[0]
+    per_core = max(256, int(single_rate * 1e9 / FLOP_PER_SITE * seconds))
+    n = int(min(V // 2, per_core * cores))
+    sites = np.random.default_rng(7).choice(V, n, replace=False)
+    tmp = tempfile.mkdtemp(prefix="qxd_oracle_")
+    try:
+        paths = {}
+        for key, arr in (("U", U), ("A", A), ("psi", psi)):
+            paths[key] = os.path.join(tmp, key + ".npy")
+            np.save(paths[key], np.ascontiguousarray(arr))
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"
+        try:
+            jobs = [dict(root=ROOT, w=w, sites=chunk, **paths) for chunk in np.array_split(sites, cores)]
+            with mp.get_context("spawn").Pool(cores) as pool:
+                res = pool.map(_oracle_worker, jobs)
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    nsites = sum(r[0] for r in res)
+    return FLOP_PER_SITE * nsites / wall / 1e9, cores, nsites, wall
+
+
 def make_inputs(w, device):
     from paper_1908_11673_gb300 import workload
     U, A = workload.gauge_field(w["L"], w["field_seed"], stout_steps=w["stout"], rho=w["rho"], device=device)
@@ -231,6 +292,7 @@ def sum_over_ranks(dist, value, device):
 def run_reference(args, w, name):
     """The oracle on the host cores: each step a bounded sample of sites."""
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return 0
     U, A, eta = make_inputs(w, "cpu")
@@ -248,7 +310,7 @@ def run_reference(args, w, name):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_desc(name, w),
+        "config": workload_desc(name, w, args, world),
         "cpu_baseline": {"value": value, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
                          "sample": f"D_w at {nsites} random sites of the workload over {args.steps} steps "
                                    f"(NumPy FP64, one process)"},
@@ -256,6 +318,88 @@ def run_reference(args, w, name):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def spectral_range(ctx, qxd, torch, dev, stream, V, n_power=40, n_inverse=5):
+    """Estimates of the extreme eigenvalues of Dhat^+ Dhat through the C ABI:
+    lambda_max by power iteration with the FP64 operator (a lower bound that
+    converges from below), lambda_min by inverse iteration with the multi-shift
+    solver at one shift sigma = 0 (the Rayleigh quotient of the last iterate, an
+    upper bound converging from above).  The printed approximation assumes the
+    spectrum of |Qhat| = sqrt(Dhat^+ Dhat) inside [r_a, r_b] (App. A.1, eq. normbound)."""
+    ne = V // 2
+    gen = torch.Generator(device=dev).manual_seed(77)
+    x = torch.randn((ne, 4, 3), dtype=torch.complex128, device=dev, generator=gen)
+    y = torch.empty_like(x)
+    t = torch.empty_like(x)
+    lam_max = 0.0
+    for _ in range(n_power):
+        x /= torch.linalg.vector_norm(x)
+        ctx.apply_Dhat_eo(0, qxd.FP64, x, t, stream=stream)
+        ctx.apply_Dhat_eo(0, qxd.FP64, t, y, dagger=True, stream=stream)
+        lam_max = float(torch.vdot(x.reshape(-1), y.reshape(-1)).real)
+        x, y = y, x
+    x = torch.randn((ne, 4, 3), dtype=torch.complex128, device=dev, generator=gen)
+    lam_min = None
+    iters = 0
+    for _ in range(n_inverse):
+        x /= torch.linalg.vector_norm(x)
+        info = ctx.solve_multishift(0, [0.0], x, y, tol=1e-10, inner=qxd.FP32, stream=stream)
+        iters += info.iters
+        # Rayleigh quotient of Dhat^+ Dhat at y = (Dhat^+ Dhat)^-1 x: <y, x> / <y, y>
+        lam_min = float(torch.vdot(y.reshape(-1), x.reshape(-1)).real / torch.vdot(y.reshape(-1), y.reshape(-1)).real)
+        x, y = y, x
+    ra, rb = 1.98e-3, 7.62  # range of the printed degree-10 approximation (App. C, [Rational 0])
+    return {"lambda_max_estimate": lam_max, "lambda_min_estimate": lam_min,
+            "power_iterations": n_power, "inverse_iterations": n_inverse, "inverse_cg_iterations": iters,
+            "printed_range_squared": [ra * ra, rb * rb],
+            "inside_printed_range": bool(lam_max <= rb * rb and lam_min >= ra * ra)}
+
+
+def batched_row(qxd, torch, dev, stream, timed):
+    """24^3 x 48 (V = 663,552, antiperiodic time, 5 stout steps, qhat = -2,
+    kappa = 0.136377): the FP32 multi-right-hand-side D_w at nrhs = 1, 4, 12
+    (algorithmic bytes per output site per right-hand side and GB/s of the hop
+    launches, CUDA events around each launch) and the ten-shift multi-shift CG of
+    the printed degree-10 approximation (FP32 Krylov space, FP64 refinement)."""
+    w = WORKLOADS["24^3x48"]
+    U, A, _ = make_inputs(w, str(dev))
+    ctx = qxd.Context(w["L"], w["cstar"], w["theta"], device=dev.index or 0)
+    ctx.set_links(U, A, w["invqel"], stream=stream)
+    ctx.set_clover(0, w["qhat"], w["kappa"], w["su3csw"], w["u1csw"], stream=stream)
+    del U, A
+    V = ctx.V
+    peak, _ = measured_peaks()
+    row = {"lattice": "24^3x48", "V": V, "mrhs": []}
+    gen = torch.Generator(device=dev).manual_seed(3)
+    for nrhs in (1, 4, 12):
+        x = torch.randn((nrhs, V, 4, 3), dtype=torch.complex64, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        ctx.apply_Dw(0, qxd.FP32, x, y, nrhs=nrhs, stream=stream)  # tunes the launch shape
+        torch.cuda.synchronize()
+        ctx.profile(2)
+        for _ in range(10):
+            ctx.apply_Dw(0, qxd.FP32, x, y, nrhs=nrhs, stream=stream)
+        hops = [p for p in ctx.profile_entries() if p["name"].startswith("hop_")]
+        ctx.profile(0)
+        ms = sum(p["ms"] for p in hops)
+        by = sum(p["bytes"] for p in hops)
+        n = sum(p["launches"] for p in hops)
+        row["mrhs"].append({"nrhs": nrhs, "hop_launches": n, "ms_per_Dw": 2 * ms / n,
+                            "bytes_per_site_per_rhs": by / n / (V // 2) / nrhs,
+                            "GBps": by / (ms * 1e-3) / 1e9, "frac_of_hbm": by / (ms * 1e-3) / 1e9 / peak,
+                            "Gflops": n * (V // 2) * nrhs * FLOP_PER_SITE / (ms * 1e-3) / 1e9})
+        del x, y
+    A_r, nu_r, mu_r = read_rational(GOLDEN_RATIONAL)
+    sigma = list(mu_r ** 2)
+    phi = torch.randn((V // 2, 4, 3), dtype=torch.complex128, device=dev, generator=gen)
+    xs = torch.empty((len(sigma), V // 2, 4, 3), dtype=torch.complex128, device=dev)
+    ctx.solve_multishift(0, sigma, phi, xs, tol=1e-10, inner=qxd.FP32, stream=stream)
+    ms_ms, inf = timed(lambda: ctx.solve_multishift(0, sigma, phi, xs, tol=1e-10, inner=qxd.FP32, stream=stream), 1)
+    row["mscg_10_shifts"] = {"ms": ms_ms, "cg_iters": inf[0].iters, "worst_shift_relres": inf[0].true_relres}
+    del phi, xs
+    ctx.close()
+    return row
 
 
 def run_native(args, w, name):
@@ -309,19 +453,27 @@ def run_native(args, w, name):
         ms = max_over_ranks(dist, e0.elapsed_time(e1), dev)
         return ms, infos
 
-    # ---- timed region: K mixed-precision solves, kernels timed by event pairs -----
+    def timed_local(fn, k):
+        """timed() without the barriers, for work that rank 0 does alone"""
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [fn() for _ in range(k)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), infos
+
+    # ---- timed region: K mixed-precision solves; launches counted, not timed --------
     sampler = ClockSampler(local)
     sampler.start()
-    ctx.profile(2)
+    ctx.profile(1)
     ms, infos = timed(lambda: ctx.solve(0, eta_d, psi_d, **solve_kw), args.steps)
-    prof = ctx.profile_entries()
+    counts = ctx.profile_entries()
     ctx.profile(0)
     clocks = sampler.stop()
-    hops = [p for p in prof if p["name"].startswith("hop_")]
-    hop_launches = sum(p["launches"] for p in hops)
+    hop_launches = sum(p["launches"] for p in counts if p["name"].startswith("hop_"))
     flops = hop_launches * (V // 2) * FLOP_PER_SITE
-    launches = sum(p["launches"] for p in prof)
-    total_ms_k = sum(p["ms"] for p in prof)
+    launches = sum(p["launches"] for p in counts)
 
     # the mixed solver's outer residual runs in double-float: check the last timed
     # solution with the FP64 operator before any other solve overwrites it
@@ -331,12 +483,20 @@ def run_native(args, w, name):
     rel64 = float(torch.linalg.vector_norm(eta_d - dpsi) / torch.linalg.vector_norm(eta_d))
     del dpsi
 
+    # ---- kernel table: the same K solves again, every launch bracketed by CUDA events
+    # recorded on its stream (a second pass, so that the events cost nothing above) ----
+    ctx.profile(2)
+    ms_prof, infos_prof = timed(lambda: ctx.solve(0, eta_d, psi_d, **solve_kw), args.steps)
+    prof = ctx.profile_entries()
+    ctx.profile(0)
+    total_ms_k = sum(p["ms"] for p in prof)
+
     # ---- e2e: pinned host buffers through the C ABI ----------------------------------
     eta_h = torch.from_numpy(eta).pin_memory()
     psi_h = torch.empty_like(eta_h).pin_memory()
     ctx.solve(0, eta_h, psi_h, **solve_kw)  # warm-up: the library's staging buffers are allocated here
-    ms_e2e, infos_e2e = timed(lambda: ctx.solve(0, eta_h, psi_h, **solve_kw), max(1, min(args.steps, 3)))
     k_e2e = max(1, min(args.steps, 3))
+    ms_e2e, infos_e2e = timed(lambda: ctx.solve(0, eta_h, psi_h, **solve_kw), k_e2e)
     e2e_value = flops / args.steps * k_e2e / (ms_e2e * 1e-3) / 1e9
 
     # ---- plain FP64 CGNE on the same system ---------------------------------------------
@@ -349,7 +509,9 @@ def run_native(args, w, name):
 
     # ---- next rows of the method on the same system (not part of the timed step) --------
     nxt = None
+    spec = None
     if not args.no_extras:
+        spec = spectral_range(ctx, qxd, torch, dev, stream, V)
         nxt = {}
         for ncy, nmr in ((5, 5), (3, 4)):
             ctx.set_sap(ncy, nmr)
@@ -391,6 +553,7 @@ def run_native(args, w, name):
         ctx.sdet(0, stream=stream)
         ms_sd, _ = timed(lambda: ctx.sdet(0, stream=stream), 3)
         nxt["sdet"] = {"ms": ms_sd / 3, "logdet_per_odd_site": ctx.sdet(0, stream=stream)[0] / (V // 2)}
+        del phi_e
 
     # ---- aggregate over ranks ----------------------------------------------------------
     total_value = sum_over_ranks(dist, flops, dev) / (ms * 1e-3) / 1e9
@@ -398,11 +561,19 @@ def run_native(args, w, name):
         ctx.close()
         dist.destroy_process_group()
         return 0
+    if not args.no_extras:
+        # the batched configuration on its own lattice (rank 0 only, after the others are done)
+        ctx.close()
+        ctx = None
+        del eta_d, psi_d
+        torch.cuda.empty_cache()
+        nxt["batched_24x24x24x48"] = batched_row(qxd, torch, dev, stream, timed_local)
 
     peak, peak_kind = measured_peaks()
     dom = max(prof, key=lambda p: p["ms"])
     mean_ms = dom["ms"] / dom["launches"]
     bytes_per_launch = dom["bytes"] / dom["launches"]
+    timing = f"CUDA events around every launch on its stream, in a second pass of the same {args.steps} solves"
     if dom["name"].startswith("hop_fp64"):
         # the FP64 hopping kernel is bound by the FP64 pipe (1/64 of the FP32 rate on
         # this GPU), not by HBM: 2112 flop per output site against the FP64 FMA peak
@@ -412,7 +583,7 @@ def run_native(args, w, name):
                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "peak_kind": "measured FP64 FMA rate of this GPU (2 flop per DFMA)",
                     "flops_per_launch": flops_per_launch, "mean_launch_ms": mean_ms,
-                    "hbm_GBps": bytes_per_launch / (mean_ms * 1e-3) / 1e9, "traffic": None}
+                    "hbm_GBps": bytes_per_launch / (mean_ms * 1e-3) / 1e9, "traffic": None, "timing": timing}
     else:
         achieved = bytes_per_launch / (mean_ms * 1e-3) / 1e9
         per_site = NCU_BYTES_PER_SITE.get(dom["name"])
@@ -420,7 +591,8 @@ def run_native(args, w, name):
                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (HBM copy bandwidth)",
                     "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_ms,
                     "traffic": per_site * (V // 2) if per_site else None,
-                    "traffic_source": "ncu dram bytes per site on 24^3x48 scaled to this lattice" if per_site else None}
+                    "traffic_source": "ncu dram bytes per site on 24^3x48 scaled to this lattice" if per_site else None,
+                    "timing": timing}
     kernels = []
     for p in sorted(prof, key=lambda p: -p["ms"]):
         gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None
@@ -429,37 +601,43 @@ def run_native(args, w, name):
                         "GB/s": round(gbs, 1) if gbs else None})
     info = infos[-1]
     tts = {"mixed_ms": ms / args.steps, "iters_inner": info.iters, "outer_restarts": info.restarts,
-           "true_relres": info.true_relres, "true_relres_fp64_check": rel64, "status": info.status}
+           "true_relres": info.true_relres, "true_relres_fp64_check": rel64, "status": info.status,
+           "profiled_pass_ms": ms_prof / args.steps, "profiled_pass_iters": infos_prof[-1].iters}
     if base:
         tts.update(base)
         tts["speedup_vs_fp64_cgne"] = base["fp64_cgne_ms"] / (ms / args.steps)
 
     cpu = None
     if not args.no_cpu_baseline:
-        Uh, Ah = U, A
-        rate, n, dt = oracle_rate(w, Uh, Ah, eta, float(os.environ.get("QXD_CPU_SECONDS", "15")))
-        cpu = {"value": rate, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
-               "sample": f"D_w at {n} random sites of the workload ({dt:.1f} s, NumPy FP64, one process)"}
+        sec = float(os.environ.get("QXD_CPU_SECONDS", "10"))
+        rate, n, dt = oracle_rate(w, U, A, eta, sec)
+        rate_all, cores, n_all, dt_all = oracle_rate_all_cores(w, U, A, eta, sec, rate)
+        cpu = {"value": rate_all, "unit": "Gflop/s", "cores": cores, "kind": "oracle",
+               "sample": f"D_w at {n_all} random sites of the workload, one spawned NumPy FP64 process per "
+                         f"core ({dt_all:.1f} s wall)",
+               "single_core": {"value": rate, "cores": 1,
+                               "sample": f"D_w at {n} random sites ({dt:.1f} s, one process)"}}
 
     line = {
         "metric": METRIC, "value": total_value, "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.inner == "fp32" else "bf16+f32+f64", "data": "synthetic",
-        "config": workload_desc(name, w) | {"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                            "nkv": args.nkv, "inner": args.inner},
+        "config": workload_desc(name, w, args, world),
         "time_to_solution": tts,
         "roofline": roofline,
-        "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "Gflop/s", "h2d_bytes_per_step": int(eta.nbytes),
                 "d2h_bytes_per_step": int(eta.nbytes), "ms_per_step": ms_e2e / k_e2e},
         "gpu_launches": launches,
-        "setup_s": setup_s,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "setup_s": setup_s,
+        "spectral_range": spec,
         "next_rows": nxt,
+        "kernels": kernels,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist:
         dist.destroy_process_group()
     return 0

@@ -5,9 +5,9 @@
  * the solvers built on it, on one NVIDIA GB300 (sm_103a).
  *
  * Definitions follow openQ*D (Campos et al., arXiv:1908.11673):
- *   operator           Sec. 2.2, eqs. dirac, wilson-dirac, frw-covder, bkw-covder
- *   SW term            Sec. 2.2, eq. sw-term and the U(1) field tensor below it
- *   even-odd operator  Sec. 2.2, definition of D-hat
+ *   operator           Sec. 2.3, eqs. dirac, wilson-dirac, frw-covder, bkw-covder
+ *   SW term            Sec. 2.3, eq. sw-term and the U(1) field tensor below it
+ *   even-odd operator  Sec. 2.3, definition of D-hat
  *   C* boundaries      Sec. 2.1, eqs. cstar-bc, ext-periodic-bc, ext-shifted-bc
  *   solvers            Sec. 4.4 (CG, MSCG, GCR); shifts of App. A.1/A.2
  *
@@ -164,7 +164,7 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream);
  * double-float, nrhs = 1.  in and out must not overlap. */
 int qxd_apply_Dw(qxd_ctx* ctx, int fl, int prec, const void* in, void* out, int nrhs, void* stream);
 
-/* out_e = Dhat in_e = (D_ee - D_eo D_oo^-1 D_oe) in_e (Sec. 2.2) on even-site
+/* out_e = Dhat in_e = (D_ee - D_eo D_oo^-1 D_oe) in_e (Sec. 2.3) on even-site
  * vectors [nrhs][V/2][4][3].  If dagger != 0 applies Dhat^+ = gamma5 Dhat gamma5. */
 int qxd_apply_Dhat_eo(qxd_ctx* ctx, int fl, int prec, int dagger, const void* in_e, void* out_e,
                       int nrhs, void* stream);
@@ -238,7 +238,7 @@ int qxd_rw_rat(qxd_ctx* ctx, int fl, const qxd_rational* r, int u, int v, int nt
 int qxd_rw_rtm(qxd_ctx* ctx, int fl, const qxd_rational* r_mu, const qxd_rational* r_t, int k, int l,
                const qxd_solver* s, const void* eta_e, double* exponent, qxd_info* info, void* stream);
 
-/* Small-determinant action (Sec. 2.2; det D = det D_oo det Dhat):
+/* Small-determinant action (Sec. 2.3; det D = det D_oo det Dhat):
  * *logdet = sum over odd sites x of log |det D_oo(x)|, D_oo(x) = 1/(2 kappa) + dD_sw
  * (12x12), in FP64 from an LDL^H factorisation of each 6x6 chiral block;
  * S_sdet = -alpha_f *logdet for a flavour of weight alpha_f.  *nneg (may be NULL)
@@ -258,10 +258,15 @@ int qxd_sdet(qxd_ctx* ctx, int fl, double* logdet, int* nneg, void* stream);
  * that array until the process exits.
  *  - Maximum size: V/2 <= 32768 even sites (e.g. 16^4, or 8x(2x8)x8x16 with C*);
  *    larger lattices return QXD_EARG.
- *  - in_e and out_e must be device arrays ([V/2][4][3] complex128 for QXD_FP64,
- *    complex64 otherwise); host arrays return QXD_EARG (staging would allocate).
+ *  - in_e and out_e must be device arrays of the context's GPU ([V/2][4][3]
+ *    complex128 for QXD_FP64, complex64 for QXD_FP32 and QXD_BF16); host arrays
+ *    and arrays on another GPU return QXD_EARG (staging would allocate).
  *  - The first call on a device looks up the array's device address with the
  *    CUDA runtime.  Make that first call before any stream capture.
+ *  - The call never runs the launch-shape autotuner of qxd_apply_Dhat_eo (which
+ *    times candidate shapes and waits for them on the host): it uses the shape
+ *    that an earlier qxd_apply_Dhat_eo on the same context and lattice tuned,
+ *    else a fixed default shape.  The result is the same either way.
  *  - Every call, from any context on the device, uses the same array.  Calls
  *    whose work overlaps on the GPU (different streams, or different threads)
  *    race and give wrong results.  Serialise them.  Each call overwrites the

@@ -1,6 +1,6 @@
 """Plain FP64 CPU oracle for the O(a)-improved Wilson-Dirac operator of
-openQ*D (Sec. 2.2, eqs. dirac, wilson-dirac, frw-covder, bkw-covder, sw-term),
-its even-odd preconditioned form (Sec. 2.2, definition of D-hat), the C*
+openQ*D (Sec. 2.3, eqs. dirac, wilson-dirac, frw-covder, bkw-covder, sw-term),
+its even-odd preconditioned form (Sec. 2.3, definition of D-hat), the C*
 orbifold geometry (Sec. 2.1) and the solvers (Sec. 4.4; App. A).
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU

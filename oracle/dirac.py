@@ -1,4 +1,4 @@
-"""O(a)-improved Wilson-Dirac operator with SU(3) x U(1) links (Sec. 2.2).
+"""O(a)-improved Wilson-Dirac operator with SU(3) x U(1) links (Sec. 2.3).
 
     D = m0 + D_w + dD_sw                      (eq. dirac, dD_b = 0 for periodic time)
     D_w = sum_mu 1/2 {gamma_mu (nabla_mu + nabla*_mu) - nabla*_mu nabla_mu}
@@ -216,7 +216,7 @@ class DiracOperator:
             out -= 0.5 * (fwd + bwd)
         return out
 
-    # --- even-odd preconditioning (Sec. 2.2, definition of D-hat) -------------
+    # --- even-odd preconditioning (Sec. 2.3, definition of D-hat) -------------
     def even_sites(self):
         return self.geom.sites(0)
 

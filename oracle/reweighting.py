@@ -1,7 +1,7 @@
 """Rational factors of the quark determinant on lattice fields: the pseudofermion
 action of a factor P_{k,l} (App. A.2, eqs. Pfactor, Spf, Spf2), the stochastic
 exponents of the reweighting factors W_rat and W_rtm (App. A.3), and the
-small-determinant action S_sdet (Sec. 2.2, even-odd preconditioning).
+small-determinant action S_sdet (Sec. 2.3, even-odd preconditioning).
 
 TEST INFRASTRUCTURE ONLY: imported by the test suite, the smoke check and the
 benchmark's CPU baseline, never by the library.  Plain FP64 NumPy.

@@ -1,7 +1,7 @@
-// Hopping kernels of the Wilson-Dirac operator (Sec. 2.2):
+// Hopping kernels of the Wilson-Dirac operator (Sec. 2.3):
 //   (H psi)(x) = -1/2 sum_mu [(1 - gamma_mu) V(x,mu) psi(x+mu) + (1 + gamma_mu) V(x-mu,mu)^+ psi(x-mu)]
 // with V = U z^qhat, evaluated for all sites of one parity from a field on the
-// other parity (even-odd preconditioning, Sec. 2.2).  One thread per output
+// other parity (even-odd preconditioning, Sec. 2.3).  One thread per output
 // site; the neighbour indices are computed on the fly from the coordinates
 // (C* shifted boundaries included); (1 -+ gamma_mu) are applied as spin
 // projections onto two-spinors before the colour multiplication.

@@ -162,10 +162,19 @@ static void launch_cfg(int prec, int self, int post, int nr, int threads, const 
 // Autotuner: candidate (NR, threads) pairs timed on the caller's own data (the
 // kernel reads in_nb/in_self and writes out, which do not overlap, so
 // repeating it is harmless); the fastest is kept for this key.
+thread_local bool t_no_autotune = false;
+
 int launch_hop_mr(qxd_ctx* ctx, int prec, const HopDev& d, const HopArgs& a, cudaStream_t st, int* nr_used) {
     const Geo& g = ctx->g;
     const auto key = std::make_tuple(prec, a.self_mode, a.post_mode, a.nrhs, (long long)g.Vh);
     auto it = ctx->tune_hop.find(key);
+    if (it == ctx->tune_hop.end() && t_no_autotune) {
+        // untuned key while tuning is off: the default shape, nothing timed or cached
+        *nr_used = 1;
+        launch_cfg(prec, a.self_mode, a.post_mode, 1, 128, g, d, a.nrhs, st);
+        QXD_CUDA(ctx, cudaGetLastError());
+        return QXD_OK;
+    }
     if (it == ctx->tune_hop.end()) {
         const int nrs[3] = {1, 2, 4};
         const int ths[3] = {64, 128, 256};

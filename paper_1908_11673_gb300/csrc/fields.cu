@@ -1,6 +1,6 @@
 // Field set-up kernels: gauge-field ingest with the C* mirror fill, per-flavour
 // hopping phases, and the site-diagonal term 1/(2 kappa) + dD_sw with its
-// inverse (Sec. 2.1 eq. cstar-bc-gauge; Sec. 2.2 eqs. frw-covder, sw-term).
+// inverse (Sec. 2.1 eq. cstar-bc-gauge; Sec. 2.3 eqs. frw-covder, sw-term).
 #include "blas.h"
 #include "qxd_internal.h"
 

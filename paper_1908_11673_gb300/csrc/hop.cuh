@@ -1,4 +1,4 @@
-// Device building blocks of the hopping term (Sec. 2.2):
+// Device building blocks of the hopping term (Sec. 2.3):
 //   (H psi)(x) = -1/2 sum_mu [(1 - gamma_mu) V(x,mu) psi(x+mu) + (1 + gamma_mu) V(x-mu,mu)^+ psi(x-mu)]
 // in the chiral basis: spin projection onto two-spinors, colour multiplication
 // by the link (FP64: stored V = U z^qhat; FP32: two rows of U rebuilt to three
@@ -208,5 +208,10 @@ QXD_HD void hop_dir(const Geo& g, const HopDev& a, const typename Prec<P>::chunk
 
 // multi-right-hand-side launcher with autotuned tile shape (dirac_mrhs.cu)
 int launch_hop_mr(qxd_ctx* ctx, int prec, const HopDev& d, const HopArgs& a, cudaStream_t st, int* nr_used);
+// While true on the calling thread, launch_hop_mr does not tune a key it has not
+// seen: it launches the default shape (one right-hand side per thread, 128
+// threads) without timing, synchronising or caching anything.  Keys tuned
+// earlier keep their cached shape.
+extern thread_local bool t_no_autotune;
 
 }  // namespace qxd

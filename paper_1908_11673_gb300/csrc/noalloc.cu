@@ -5,6 +5,7 @@
 // cudaMalloc on first use.
 #include <mutex>
 
+#include "hop.cuh"
 #include "ops.h"
 #include "qxd_internal.h"
 
@@ -42,14 +43,25 @@ int scratch_address(qxd_ctx* ctx, int device, unsigned char** out) {
     return QXD_OK;
 }
 
-bool on_device(const void* p) {
+// true for device (or managed) memory of `device` itself; memory of another GPU
+// is refused, since the kernels would then read and write it over the peer link
+bool on_device(const void* p, int device) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
+
+// Turns the hop autotuner off on this thread for the lifetime of the object: a
+// first call for a new (precision, lattice) key would otherwise time candidate
+// launch shapes, which creates events and waits for them on the host.
+struct NoAutotune {
+    bool saved;
+    NoAutotune() : saved(t_no_autotune) { t_no_autotune = true; }
+    ~NoAutotune() { t_no_autotune = saved; }
+};
 
 }  // namespace
 
@@ -67,8 +79,9 @@ extern "C" int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dag
         cudaGetLastError();
         return qxd_fail(ctx, QXD_ECUDA, "apply_Dhat_eo_noalloc: cannot select the context's device");
     }
-    if (!in_e || !out_e || !on_device(in_e) || !on_device(out_e))
-        return qxd_fail(ctx, QXD_EARG, "apply_Dhat_eo_noalloc: in_e and out_e must be device arrays");
+    if (!in_e || !out_e || !on_device(in_e, ctx->device) || !on_device(out_e, ctx->device))
+        return qxd_fail(ctx, QXD_EARG,
+                        "apply_Dhat_eo_noalloc: in_e and out_e must be device arrays of the context's GPU");
     unsigned char* scratch;
     QXD_TRY(scratch_address(ctx, ctx->device, &scratch));
     // three consecutive half-lattice fields; every kernel below overwrites its
@@ -78,6 +91,7 @@ extern "C" int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dag
     void* oe = scratch + 2 * kNoallocFieldBytes;
     cudaStream_t st = (cudaStream_t)stream;
     const int cprec = prec == QXD_FP64 ? 0 : 1;
+    NoAutotune frozen;
     QXD_TRY(launch_pack(ctx, cprec, in_e, 0, 0, prec, ie, 1, st));
     QXD_TRY(op_Dhat(ctx, fl, prec, dagger ? 1 : 0, ie, oe, to, st, 1));
     QXD_TRY(launch_unpack(ctx, prec, oe, 0, cprec, out_e, 0, 1, st));

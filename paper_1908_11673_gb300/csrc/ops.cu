@@ -1,4 +1,4 @@
-// Operator compositions (Sec. 2.2): D, Dhat = D_ee - D_eo D_oo^-1 D_oe, the
+// Operator compositions (Sec. 2.3): D, Dhat = D_ee - D_eo D_oo^-1 D_oe, the
 // even-odd source and the odd-site reconstruction, each as one or two launches
 // of the hopping kernel with a fused site-diagonal prologue or epilogue.
 #include "blas.h"

@@ -2,7 +2,7 @@
 // them (App. A.1-A.3): the factor P_{k,l} (eq. Pfactor) through its partial
 // fractions, the pseudofermion action of a factor (eq. Spf2), the series terms
 // of the W_rat exponent (eqs. Wrat2, Wrat3) and the exponent of the W_rtm
-// estimate (App. A.3), plus the small-determinant action (Sec. 2.2).
+// estimate (App. A.3), plus the small-determinant action (Sec. 2.3).
 //
 // Every shifted inverse comes from one multi-shift CG over all the shifts a
 // call needs (FP32 Krylov space, then FP64 defect correction of each shift to

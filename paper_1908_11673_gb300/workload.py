@@ -12,7 +12,11 @@ Recipe (all FP64, NumPy PCG64 streams):
   * U(1) angles A_mu(x) ~ N(0, sigma_a^2) (the compact field z = exp(iA) of Sec. 2).
   * Optional stout smearing of the SU(3) links (Morningstar-Peardon, isotropic,
     staples from all nu != mu, parameter rho) with periodic identification of the
-    physical lattice; the U(1) angles are not smeared.
+    physical lattice.
+  * Optional stout smearing of the U(1) links, the abelian case of the same
+    recipe: z(x,mu) <- exp(i rho Im[C(x,mu) z(x,mu)^*]) z(x,mu) with C the sum of
+    the six staples, i.e. A_mu(x) <- A_mu(x) + rho sum_staples sin(theta_staple - A_mu(x)),
+    all directions updated at once.  Off by default (u1_stout_steps = 0).
   * Sources: complex Gaussian, real and imaginary parts N(0, 1).
 
 Field layout: physical lattice, lexicographic site index with x0 (time) slowest,
@@ -77,12 +81,34 @@ def _stout_step(U: torch.Tensor, L, rho: float) -> torch.Tensor:
     return new
 
 
+def _u1_stout_step(A: torch.Tensor, rho: float) -> torch.Tensor:
+    """One abelian stout step on the angles A [L0,L1,L2,L3,4] (periodic)."""
+    new = torch.empty_like(A)
+    for mu in range(4):
+        Amu = A[..., mu]
+        s = torch.zeros_like(Amu)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            Anu = A[..., nu]
+            # staple through x + nu: A_nu(x) + A_mu(x+nu) - A_nu(x+mu)
+            up = Anu + torch.roll(Amu, -1, dims=nu) - torch.roll(Anu, -1, dims=mu)
+            # staple through x - nu: -A_nu(x-nu) + A_mu(x-nu) + A_nu(x-nu+mu)
+            Anu_m = torch.roll(Anu, 1, dims=nu)
+            dn = -Anu_m + torch.roll(Amu, 1, dims=nu) + torch.roll(Anu_m, -1, dims=mu)
+            s = s + torch.sin(up - Amu) + torch.sin(dn - Amu)
+        new[..., mu] = Amu + rho * s
+    return new
+
+
 def gauge_field(L, seed: int, sigma_h: float = 0.3, sigma_a: float = 0.2,
-                stout_steps: int = 0, rho: float = 0.1, device: str | None = None):
+                stout_steps: int = 0, rho: float = 0.1, device: str | None = None,
+                u1_stout_steps: int = 0):
     """Return (U, A) on the physical lattice L=(L0,L1,L2,L3) as NumPy arrays.
 
     The random draws come from PCG64(seed) on the host; the exponentials and the
     smearing run in torch on `device` (CUDA when available unless given).
+    u1_stout_steps > 0 smears the U(1) angles as well (same rho).
     """
     L = tuple(int(v) for v in L)
     V = int(np.prod(L))
@@ -97,7 +123,21 @@ def gauge_field(L, seed: int, sigma_h: float = 0.3, sigma_a: float = 0.2,
     for _ in range(int(stout_steps)):
         U = _stout_step(U, L, rho)
     U = U.reshape(V, 4, 3, 3).cpu().numpy()
+    if u1_stout_steps:
+        A = u1_stout(A, L, u1_stout_steps, rho, device)
     return np.ascontiguousarray(U), np.ascontiguousarray(A)
+
+
+def u1_stout(A: np.ndarray, L, steps: int, rho: float = 0.1, device: str | None = None) -> np.ndarray:
+    """The U(1) angles A [V][4] on the physical lattice L after `steps` abelian
+    stout steps with parameter rho (periodic identification)."""
+    L = tuple(int(v) for v in L)
+    if device is None:
+        device = "cuda" if torch.cuda.is_available() else "cpu"
+    At = torch.from_numpy(np.asarray(A, dtype=np.float64)).to(device).reshape(*L, 4)
+    for _ in range(int(steps)):
+        At = _u1_stout_step(At, rho)
+    return np.ascontiguousarray(At.reshape(-1, 4).cpu().numpy())
 
 
 def unit_gauge_field(L):

@@ -61,3 +61,18 @@ def test_single_process_aggregation():
     import bench
     assert bench.max_over_ranks(None, 3.0, "cpu") == 3.0
     assert bench.sum_over_ranks(None, 2.0, "cpu") == 2.0
+
+
+def test_all_core_oracle_rate():
+    """The all-core CPU baseline: spawned workers, memory-mapped fields, the
+    wall time of the parallel region (8^4, a fraction of a second of work)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_1908_11673_gb300 import workload
+    w = bench.WORKLOADS["8^4"]
+    U, A = workload.gauge_field(w["L"], w["field_seed"], device="cpu")
+    psi = workload.spinor(4096, 1)
+    rate, cores, n, wall = bench.oracle_rate_all_cores(w, U, A, psi, 0.05, 0.02)
+    assert cores == len(os.sched_getaffinity(0))
+    assert 0 < n <= 2048 and wall > 0 and rate > 0

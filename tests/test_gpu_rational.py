@@ -1,5 +1,5 @@
 """Rational factors, reweighting exponents and the small determinant on the GPU
-(App. A.2, A.3; Sec. 2.2) against the oracle (oracle/reweighting.py) on the
+(App. A.2, A.3; Sec. 2.3) against the oracle (oracle/reweighting.py) on the
 same seeded fields.
 
 Tolerances.  Both sides take every shifted inverse from a multi-shift CG to a

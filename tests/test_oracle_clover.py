@@ -1,5 +1,5 @@
 """Pins of the SW term normalisation (eq. sw-term and the U(1) field tensor of
-Sec. 2.2) by a constant abelian flux.
+Sec. 2.3) by a constant abelian flux.
 
 On a torus, the U(1) field z_2(x) = exp(i phi x1) for 0 <= x1 < L1, and
 z_1(x) = exp(-i phi L1 x2) on the links leaving x1 = L1 - 1 (1 elsewhere) with
@@ -74,7 +74,7 @@ def test_su3_sw_term_constant_flux():
 
 
 def test_sw_term_is_hermitian_and_chirally_block_diagonal():
-    """The field tensors are anti-Hermitian (Sec. 2.2), so dD_sw is Hermitian, and
+    """The field tensors are anti-Hermitian (Sec. 2.3), so dD_sw is Hermitian, and
     sigma_{mu nu} commutes with gamma_5: the 12x12 term splits into two 6x6
     blocks of definite chirality (the structure the CUDA path stores)."""
     from oracle.dirac import GAMMA5

@@ -1,5 +1,5 @@
 """Dense brute force on small lattices: the even-odd (Schur) identities behind
-Dhat (Sec. 2.2) and the solvers (Sec. 4.4) against LAPACK."""
+Dhat (Sec. 2.3) and the solvers (Sec. 4.4) against LAPACK."""
 import numpy as np
 import pytest
 

@@ -1,5 +1,5 @@
 """Pins of the oracle against closed forms of the free and constant-background
-operator (Sec. 2.1 boundary conditions, Sec. 2.2 operator).
+operator (Sec. 2.1 boundary conditions, Sec. 2.3 operator).
 
 Free field, U = 1, z = 1: a plane wave psi(x) = exp(i p.x) chi is an
 eigenfunction of the hopping term and

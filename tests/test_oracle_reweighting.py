@@ -1,5 +1,5 @@
 """Pins of the rational factors on lattice fields (App. A.2, A.3) and of the
-small-determinant action (Sec. 2.2), against what the mathematics fixes:
+small-determinant action (Sec. 2.3), against what the mathematics fixes:
 
  * the residues of Ptilde_{k,l} - 1 reproduce the product form at arbitrary q2
    (and vanish when both approximations are the same);
