@@ -1,6 +1,6 @@
 """O(a)-improved Wilson-Dirac operator with SU(3) x U(1) links (Sec. 2.3).
 
-    D = m0 + D_w + dD_sw                      (eq. dirac, dD_b = 0 for periodic time)
+    D = m0 + D_w + dD_sw + dD_b               (eq. dirac; dD_b = 0 for periodic time)
     D_w = sum_mu 1/2 {gamma_mu (nabla_mu + nabla*_mu) - nabla*_mu nabla_mu}
     nabla_mu  psi(x) = U(x,mu) z(x,mu)^qhat psi(x+mu) - psi(x)            (eq. frw-covder)
     nabla*_mu psi(x) = psi(x) - U(x-mu,mu)^+ z(x-mu,mu)^-qhat psi(x-mu)    (eq. bkw-covder)
@@ -20,6 +20,14 @@ Expanding the covariant derivatives gives, site by site,
 
 which is what `DiracOperator.apply` evaluates literally, with explicit 4x4
 gamma matrices and 3x3 colour products.
+
+Open time boundary (the definition the paper defers to openQCD; Luescher and
+Schaefer, Comput. Phys. Commun. 184 (2013) 519): the fields live on
+0 <= x0 <= L0 - 1, the hops that would cross the boundary are absent (phase 0
+from Geometry.neighbour), the clover leaves whose plaquette would cross it are
+absent from Fhat and Ahat, and
+    dD_b psi(x) = (cF - 1) (delta_{x0,0} + delta_{x0,L0-1}) psi(x),
+with cF the boundary improvement coefficient (tree level cF = 1: dD_b = 0).
 
 Readings where the paper is silent (each used identically by every test):
   * gamma basis: chiral Euclidean basis, gamma_0 = [[0,-1],[-1,0]],
@@ -148,7 +156,10 @@ class DiracOperator:
         leaf2 = U(x, nu) @ dag(U(xmm_pn, mu)) @ dag(U(xmm, nu)) @ U(xmm, mu)
         leaf3 = dag(U(xmm, mu)) @ dag(U(xmm_mn, nu)) @ U(xmm_mn, mu) @ U(xmn, nu)
         leaf4 = dag(U(xmn, nu)) @ U(xmn, mu) @ U(xmn_pm, nu) @ dag(U(x, mu))
-        Q = leaf1 + leaf2 + leaf3 + leaf4
+        # leaf k is the plaquette with lower corner x, x-mu, x-mu-nu, x-nu
+        inside = self.geom.plaquette_inside
+        w = [inside(c, mu, nu)[:, None, None] for c in (x, xmm, xmm_mn, xmn)]
+        Q = w[0] * leaf1 + w[1] * leaf2 + w[2] * leaf3 + w[3] * leaf4
         return (Q - dag(Q)) / 8.0
 
     def zplaq(self, idx, mu, nu):
@@ -162,8 +173,7 @@ class DiracOperator:
         xmm = self._nb(idx, mu, -1)
         xmn = self._nb(idx, nu, -1)
         xmmn = self._nb(xmm, nu, -1)
-        s = (self.zplaq(idx, mu, nu) + self.zplaq(xmm, mu, nu)
-             + self.zplaq(xmn, mu, nu) + self.zplaq(xmmn, mu, nu))
+        s = sum(self.geom.plaquette_inside(c, mu, nu) * self.zplaq(c, mu, nu) for c in (idx, xmm, xmn, xmmn))
         return 1j / (4.0 * self.g.qel) * s.imag
 
     def sw_term(self, idx):
@@ -181,7 +191,7 @@ class DiracOperator:
         return M.reshape(n, 12, 12)
 
     def diag_term(self, idx):
-        """Site-diagonal part m0 + 4 + dD_sw = 1/(2 kappa) + dD_sw (12x12).
+        """Site-diagonal part m0 + 4 + dD_sw + dD_b = 1/(2 kappa) + dD_sw + dD_b (12x12).
 
         It depends on the gauge field only, so once a large part of the lattice
         is asked for, it is computed for every site and kept."""
@@ -193,7 +203,8 @@ class DiracOperator:
         return self._diag_at(idx)
 
     def _diag_at(self, idx):
-        return self.sw_term(idx) + np.eye(12) / (2.0 * self.fl.kappa)
+        dDb = (self.geom.cF - 1.0) * self.geom.boundary_slice(idx)  # dD_b (open boundary)
+        return self.sw_term(idx) + (1.0 / (2.0 * self.fl.kappa) + dDb)[:, None, None] * np.eye(12)
 
     # --- the operator ---------------------------------------------------------
     def apply(self, psi, sites=None):

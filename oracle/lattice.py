@@ -13,6 +13,13 @@ Neighbours on the extended lattice:
     and a spinor picks up exp(+-i theta_mu) when it is transported across the
     boundary (eq. periodic-bc-quark).  theta must vanish in the spatial
     directions when C* is on (Sec. 2.1); theta_0 = pi gives antiperiodic time.
+  * open time boundary (tbc = "open"; the paper lists open and SF boundaries in
+    time, Sec. 2.3 eq. dirac, and defers their definition to openQCD, Luescher
+    and Schaefer, Comput. Phys. Commun. 184 (2013) 519): the lattice ends at
+    x0 = 0 and x0 = L0 - 1.  Nothing is transported across: the phase of a step
+    across the time boundary is 0, and a plaquette in a plane containing time
+    whose lower corner has x0 = L0 - 1 does not exist (plaquette_inside).  The
+    boundary improvement coefficient cF enters dD_b (dirac.py).
 
 Site index: lexicographic with x0 slowest, idx = ((x0*N1 + x1)*N2 + x2)*N3 + x3
 where N = extended extents.  Parity = (x0 + x1 + x2 + x3) mod 2 (0 = even).
@@ -26,10 +33,16 @@ import numpy as np
 
 
 class Geometry:
-    def __init__(self, L, cstar: int = 0, theta=(0.0, 0.0, 0.0, 0.0)):
+    def __init__(self, L, cstar: int = 0, theta=(0.0, 0.0, 0.0, 0.0), tbc: str = "periodic", cF: float = 1.0):
         self.L = tuple(int(v) for v in L)
         self.cstar = int(cstar)
         self.theta = tuple(float(t) for t in theta)
+        self.tbc = str(tbc)
+        self.cF = float(cF)
+        if self.tbc not in ("periodic", "open"):
+            raise ValueError("tbc must be 'periodic' or 'open'")
+        if self.tbc == "open" and self.theta[0] != 0.0:
+            raise ValueError("theta_0 must vanish with an open time boundary")
         if not 0 <= self.cstar <= 3:
             raise ValueError("cstar must be 0..3")
         if any(v <= 0 or v % 2 for v in self.L):
@@ -76,12 +89,31 @@ class Geometry:
         crossed = (x[mu] < 0) | (x[mu] >= N[mu])
         x[mu] %= N[mu]
         shifted = self.cstar >= 1 and mu >= 2 and mu <= self.cstar
-        if shifted:
+        if mu == 0 and self.tbc == "open":
+            # open boundary: no transport across x0 = L0 - 1 <-> 0
+            phase = np.where(crossed, 0.0 + 0j, 1.0 + 0j)
+        elif shifted:
             # eq. ext-shifted-bc: x + L_k e_k is identified with x + L_1 e_1
             x[1] = np.where(crossed, (x[1] + self.L[1]) % N[1], x[1])
         elif not (self.cstar >= 1 and mu == 1):
             phase = np.where(crossed, np.exp(1j * sign * self.theta[mu]), 1.0 + 0j)
         return self.index(x), phase
+
+    def plaquette_inside(self, corner, mu: int, nu: int):
+        """True for the plaquettes (lower corner `corner`, plane mu nu) that lie on
+        the lattice: all of them unless the time boundary is open, where those in
+        a plane containing time with corner x0 = L0 - 1 would cross it."""
+        corner = np.asarray(corner, dtype=np.int64)
+        if self.tbc != "open" or (mu != 0 and nu != 0):
+            return np.ones(corner.shape, dtype=bool)
+        return self.coords(corner)[0] != self.N[0] - 1
+
+    def boundary_slice(self, idx):
+        """True on the time slices x0 = 0 and x0 = L0 - 1 of an open lattice."""
+        if self.tbc != "open":
+            return np.zeros(np.shape(idx), dtype=bool)
+        x0 = self.coords(idx)[0]
+        return (x0 == 0) | (x0 == self.N[0] - 1)
 
     def translate(self, idx, shift):
         """Site idx + shift (an extended-lattice vector) on the extended torus."""
