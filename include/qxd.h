@@ -72,11 +72,25 @@ typedef enum { QXD_PRECOND_NONE = 0, QXD_PRECOND_LEARNED = 1, QXD_PRECOND_SAP = 
  * cstar in 0..3: C* boundary conditions in directions 1..cstar.
  * theta[mu]: fermion phase psi(x + L_mu e_mu) = exp(i theta_mu) psi(x)
  * (eq. periodic-bc-quark); theta[0] = pi gives antiperiodic time.  With
- * cstar > 0 the spatial phases theta[1..3] must be 0 (Sec. 2.1). */
+ * cstar > 0 the spatial phases theta[1..3] must be 0 (Sec. 2.1).
+ * tbc: time boundary, QXD_TBC_PERIODIC (phase theta[0]) or QXD_TBC_OPEN.  The
+ *   paper lists open boundaries in time among those of eq. dirac (term dD_b,
+ *   Sec. 2.3) and defers their definition to openQCD (Luescher and Schaefer,
+ *   Comput. Phys. Commun. 184 (2013) 519); this library implements: the lattice
+ *   ends at x0 = 0 and x0 = L0 - 1, no hop crosses between them, the clover
+ *   leaves (SU(3) and U(1)) whose plaquette would cross are absent from the SW
+ *   term, and dD_b psi(x) = (cF - 1)(delta_{x0,0} + delta_{x0,L0-1}) psi(x).
+ *   With QXD_TBC_OPEN theta[0] must be 0.
+ * cF: boundary improvement coefficient of dD_b (1 = tree level, dD_b = 0);
+ *   used only with QXD_TBC_OPEN. */
+typedef enum { QXD_TBC_PERIODIC = 0, QXD_TBC_OPEN = 1 } qxd_tbc;
+
 typedef struct {
     int L[4];
     int cstar;
     double theta[4];
+    int tbc;
+    double cF;
 } qxd_geom;
 
 /* One quark flavour (input-file section [Flavour n], App. C):
@@ -132,8 +146,10 @@ typedef struct {
 typedef struct qxd_ctx qxd_ctx;
 
 /* Create a context on CUDA device `device` for geometry `g`.
- * Errors: QXD_EARG for an odd or non-positive extent, cstar outside 0..3, or a
- * non-zero spatial theta with cstar > 0; QXD_ECUDA if the device is unusable. */
+ * Errors: QXD_EARG for an odd or non-positive extent, cstar outside 0..3, a
+ * non-zero spatial theta with cstar > 0, tbc outside 0..1, or an open time
+ * boundary with theta[0] != 0 or a non-finite cF; QXD_ECUDA if the device is
+ * unusable. */
 int qxd_create(const qxd_geom* g, int device, qxd_ctx** out);
 
 /* Free every device buffer of the context.  NULL is allowed. */
@@ -150,14 +166,15 @@ void qxd_destroy(qxd_ctx* ctx);
 int qxd_set_links(qxd_ctx* ctx, const double* U, const double* A, double invqel, void* stream);
 
 /* Build, for flavour slot fl (0..7), the hopping phases z^qhat (with the
- * boundary phases folded in), the site-diagonal term 1/(2 kappa) + dD_sw
+ * boundary phases folded in), the site-diagonal term 1/(2 kappa) + dD_sw + dD_b
  * (eq. sw-term; two Hermitian 6x6 chiral blocks per site) and its inverse on
  * every site, in FP64 with FP32 and BF16 copies.
  * Errors: QXD_ESTATE before qxd_set_links; QXD_EARG for fl outside 0..7 or
  * kappa <= 0; QXD_ENAN if a diagonal block is singular.  Synchronises `stream`. */
 int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream);
 
-/* out = D in on the full simulated lattice (eq. dirac with dD_b = 0), for nrhs
+/* out = D in on the full simulated lattice (eq. dirac; dD_b = 0 unless the time
+ * boundary is open, see qxd_geom), for nrhs
  * right-hand sides.  in, out: [nrhs][V][4][3] complex128 (prec = QXD_FP64) or
  * complex64 (QXD_FP32, and QXD_BF16 which stores spinors in bfloat16 inside the
  * kernel and accumulates in FP32); QXD_DF64: complex128 like QXD_FP64, arithmetic in

@@ -136,6 +136,8 @@ bool make_geo(const qxd_geom* g, Geo* G) {
         if (g->L[mu] < 2 || (g->L[mu] & 1)) return false;
     if (g->cstar < 0 || g->cstar > 3) return false;
     if (g->cstar > 0 && (g->theta[1] != 0.0 || g->theta[2] != 0.0 || g->theta[3] != 0.0)) return false;
+    if (g->tbc != QXD_TBC_PERIODIC && g->tbc != QXD_TBC_OPEN) return false;
+    if (g->tbc == QXD_TBC_OPEN && (g->theta[0] != 0.0 || !std::isfinite(g->cF))) return false;
     long long V = 1;
     for (int mu = 0; mu < 4; ++mu) V *= g->L[mu];
     if (g->cstar) V *= 2;
@@ -148,6 +150,7 @@ bool make_geo(const qxd_geom* g, Geo* G) {
     G->cstar = g->cstar;
     G->V = V;
     G->Vh = (int)(V / 2);
+    G->open0 = g->tbc == QXD_TBC_OPEN;
     return true;
 }
 

@@ -86,10 +86,13 @@ __global__ void k_set_links(Geo g, int L1phys, int L2, int L3, const double2* __
     long long phys = (((long long)x[0] * L1phys + x1) * L2 + x[2]) * L3 + x[3];
     const size_t Vh = g.Vh;
     for (int mu = 0; mu < 4; ++mu) {
+        // open time boundary: the time link leaving x0 = N0 - 1 would cross it; held
+        // as zero, so that no hop and no clover leaf uses it
+        const bool cut = g.open0 && mu == 0 && x[0] == g.N[0] - 1;
         double2 u[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            u[k] = Uin[(phys * 4 + mu) * 9 + k];
+            u[k] = cut ? make_double2(0.0, 0.0) : Uin[(phys * 4 + mu) * 9 + k];
             if (mirror) u[k].y = -u[k].y;  // U(x + L1 e1) = U(x)^*
             U64[(size_t)p * 36 * Vh + (size_t)(mu * 9 + k) * Vh + h] = u[k];
         }
@@ -196,6 +199,8 @@ QXD_HD double u1_im_sum(const Geo& g, const double* __restrict__ A64, const int 
     step(g, ys[1], nu, -1, ys[3]);
     double s = 0.0;
     for (int i = 0; i < 4; ++i) {
+        // open time boundary: a plaquette of a time plane with corner x0 = N0 - 1 is absent
+        if (g.open0 && mu == 0 && ys[i][0] == g.N[0] - 1) continue;
         int ypm[4], ypn[4];
         step(g, ys[i], mu, +1, ypm);
         step(g, ys[i], nu, +1, ypn);
@@ -265,7 +270,8 @@ QXD_HD void store_packed(const double pk[36], int blk, int p, int h, size_t Vh, 
             make_float4((float)pk[4 * k], (float)pk[4 * k + 1], (float)pk[4 * k + 2], (float)pk[4 * k + 3]);
 }
 
-__global__ void k_clover(Geo g, int qhat, double kappa, double su3csw, double u1csw, const double2* __restrict__ U64,
+__global__ void k_clover(Geo g, int qhat, double kappa, double su3csw, double u1csw, double cF,
+                         const double2* __restrict__ U64,
                          const double* __restrict__ A64, double2* __restrict__ A_64, float4* __restrict__ A_32,
                          double2* __restrict__ Ai_64, float4* __restrict__ Ai_32, int* __restrict__ flag) {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,7 +313,8 @@ __global__ void k_clover(Geo g, int qhat, double kappa, double su3csw, double u1
                 }
             }
         }
-    const double m0 = 0.5 / kappa;
+    // 1/(2 kappa), plus dD_b = cF - 1 on the slices x0 = 0 and x0 = N0 - 1 of an open lattice
+    const double m0 = 0.5 / kappa + ((g.open0 && (x[0] == 0 || x[0] == g.N[0] - 1)) ? cF - 1.0 : 0.0);
     for (int c = 0; c < 2; ++c) {
         C64 m[36];
         const M3& E1 = E[c][0];
@@ -349,7 +356,8 @@ int launch_set_flavour(qxd_ctx* ctx, int fl, cudaStream_t st) {
     dim3 grid64(nblocks(g.Vh, 64), 2);
     {
     ProfScope prof(ctx, "set_clover", (double)g.V * (4 * 144 + 4 * 8 + 2 * (576 + 288)), st);
-    k_clover<<<grid64, 64, 0, st>>>(g, F.f.qhat, F.f.kappa, F.f.su3csw, F.f.u1csw, ctx->U64, ctx->A64, F.C64[0],
+    k_clover<<<grid64, 64, 0, st>>>(g, F.f.qhat, F.f.kappa, F.f.su3csw, F.f.u1csw, ctx->geom.cF, ctx->U64, ctx->A64,
+                                  F.C64[0],
                                   F.C32[0], F.C64[1], F.C32[1], ctx->dev_flag);
     }
     QXD_CUDA(ctx, cudaGetLastError());

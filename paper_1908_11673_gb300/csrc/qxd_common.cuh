@@ -88,6 +88,7 @@ struct Geo {
     int cstar;  // C* in directions 1..cstar
     int Vh;     // V/2
     long long V;
+    int open0;  // open time boundary: no hop and no clover leaf across x0 = N0 - 1 <-> 0
 };
 
 // coordinates of the site with half index h and parity p

@@ -19,6 +19,7 @@ LIBPATH = os.path.join(HERE, "libqxd.so")
 FP64, FP32, BF16 = 0, 1, 2
 CGNE, FGCR, MSCG = 0, 1, 2
 PRECOND_NONE, PRECOND_LEARNED, PRECOND_SAP, PRECOND_DFL = 0, 1, 2, 3
+TBC_PERIODIC, TBC_OPEN = 0, 1
 
 STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: "QXD_ENAN",
           5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
@@ -39,7 +40,8 @@ class QxdError(RuntimeError):
 
 
 class Geom(ctypes.Structure):
-    _fields_ = [("L", ctypes.c_int * 4), ("cstar", ctypes.c_int), ("theta", ctypes.c_double * 4)]
+    _fields_ = [("L", ctypes.c_int * 4), ("cstar", ctypes.c_int), ("theta", ctypes.c_double * 4),
+                ("tbc", ctypes.c_int), ("cF", ctypes.c_double)]
 
 
 class Flavour(ctypes.Structure):
@@ -166,7 +168,8 @@ def rtm_residues(r_mu, r_t, k, l):
 def block_neighbours(L, cstar=0, theta=(np.pi, 0.0, 0.0, 0.0)):
     """Block neighbour table [Nb][9] of the 4^4 block grid (host code of the library)."""
     lib = load_library()
-    g = Geom((ctypes.c_int * 4)(*[int(x) for x in L]), int(cstar), (ctypes.c_double * 4)(*[float(t) for t in theta]))
+    g = Geom((ctypes.c_int * 4)(*[int(x) for x in L]), int(cstar), (ctypes.c_double * 4)(*[float(t) for t in theta]),
+             TBC_PERIODIC, 1.0)
     nb = ctypes.c_int()
     rc = lib.qxd_block_neighbours(ctypes.byref(g), None, ctypes.byref(nb))
     if rc:
@@ -202,12 +205,14 @@ def _stream(s):
 class Context:
     """One lattice on one GPU (qxd_create ... qxd_destroy)."""
 
-    def __init__(self, L, cstar=0, theta=(0.0, 0.0, 0.0, 0.0), device=0):
+    def __init__(self, L, cstar=0, theta=(0.0, 0.0, 0.0, 0.0), device=0, tbc=TBC_PERIODIC, cF=1.0):
         self.lib = load_library()
         g = Geom()
         g.L[:] = [int(v) for v in L]
         g.cstar = int(cstar)
         g.theta[:] = [float(t) for t in theta]
+        g.tbc = int(tbc)
+        g.cF = float(cF)
         self._h = ctypes.c_void_p()
         rc = self.lib.qxd_create(ctypes.byref(g), int(device), ctypes.byref(self._h))
         if rc != 0:

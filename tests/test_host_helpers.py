@@ -67,3 +67,14 @@ def test_block_neighbours_match_oracle(lib, L, cstar):
 def test_block_neighbours_rejects(lib, L):
     with pytest.raises(qxd.QxdError):
         qxd.block_neighbours(L)
+
+
+def test_geometry_validation_of_the_time_boundary(lib):
+    """qxd_create checks the geometry before it touches a device: an open time
+    boundary with a time phase, an unknown boundary type and a non-finite cF are
+    refused with QXD_EARG."""
+    for theta, tbc, cF in (((np.pi, 0, 0, 0), qxd.TBC_OPEN, 1.0), ((0, 0, 0, 0), 2, 1.0),
+                           ((0, 0, 0, 0), qxd.TBC_OPEN, float("nan"))):
+        with pytest.raises(qxd.QxdError) as e:
+            qxd.Context((4, 4, 4, 4), 0, theta, tbc=tbc, cF=cF)
+        assert e.value.code == 1
