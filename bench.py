@@ -356,6 +356,44 @@ def spectral_range(ctx, qxd, torch, dev, stream, V, n_power=40, n_inverse=5):
             "inside_printed_range": bool(lam_max <= rb * rb and lam_min >= ra * ra)}
 
 
+def learned_row(ctx, qxd, torch, dev, stream, timed, w, V, fp64_cgne_ms):
+    """The mixed-precision, batched, learned-preconditioned solve on the bench
+    system: the network (4 layers x 8 channels) is trained on four 16 x 8^3 lattices
+    with the bench system's couplings, boundary conditions and smearing (the
+    network is local and gauge covariant, so its weights carry over to the large
+    lattice), then FGCR(16) with FP32 inner solves and the network as right
+    preconditioner solves 4 right-hand sides in lockstep (one multi-right-hand-side
+    operator launch per iteration) to the true FP64 residual 1e-10; beside it the
+    same batch without the network, and the plain FP64 CGNE time per right-hand side."""
+    from paper_1908_11673_gb300 import learned
+    field = dict(L=(16, 8, 8, 8), cstar=w["cstar"], theta=w["theta"], qhat=w["qhat"], kappa=w["kappa"],
+                 su3csw=w["su3csw"], u1csw=w["u1csw"], invqel=w["invqel"], stout=w["stout"], rho=w["rho"])
+    nl, nch, nrhs = 4, 8, 4
+    W, summ = learned.train(field, [7000 + i for i in range(4)], 50, epochs=4, batch=10, nlayers=nl, nch=nch,
+                            device=dev.index or 0)
+    ctx.set_precond_weights(0, W, nl, nch)
+    gen = torch.Generator(device=dev).manual_seed(2002)
+    eta = torch.randn((nrhs, V, 4, 3), dtype=torch.complex128, device=dev, generator=gen)
+    psi = torch.empty_like(eta)
+    row = {"training": {k: v for k, v in summ.items() if k != "loss_history"}, "nrhs": nrhs}
+    for name, pre in (("learned", qxd.PRECOND_LEARNED), ("none", qxd.PRECOND_NONE)):
+        kw = dict(kind=qxd.FGCR, tol=1e-10, inner=qxd.FP32, nkv=16, precond=pre, nrhs=nrhs, nmx=100000,
+                  stream=stream)
+        ms, inf = timed(lambda: ctx.solve(0, eta, psi, **kw), 1)
+        chk = torch.empty_like(psi)
+        ctx.apply_Dw(0, qxd.FP64, psi, chk, nrhs=nrhs, stream=stream)
+        rel = [float(torch.linalg.vector_norm(eta[j] - chk[j]) / torch.linalg.vector_norm(eta[j]))
+               for j in range(nrhs)]
+        del chk
+        row[name] = {"ms": ms, "ms_per_rhs": ms / nrhs, "iters": inf[0].iters, "true_relres": inf[0].true_relres,
+                     "fp64_check_worst": max(rel), "status": inf[0].status}
+    if fp64_cgne_ms:
+        row["fp64_cgne_ms_per_rhs"] = fp64_cgne_ms
+        row["speedup_learned_vs_fp64_cgne"] = fp64_cgne_ms / row["learned"]["ms_per_rhs"]
+    del eta, psi
+    return row
+
+
 def batched_row(qxd, torch, dev, stream, timed):
     """24^3 x 48 (V = 663,552, antiperiodic time, 5 stout steps, qhat = -2,
     kappa = 0.136377): the FP32 multi-right-hand-side D_w at nrhs = 1, 4, 12
@@ -554,6 +592,8 @@ def run_native(args, w, name):
         ms_sd, _ = timed(lambda: ctx.sdet(0, stream=stream), 3)
         nxt["sdet"] = {"ms": ms_sd / 3, "logdet_per_odd_site": ctx.sdet(0, stream=stream)[0] / (V // 2)}
         del phi_e
+        nxt["learned_batched_mixed"] = learned_row(ctx, qxd, torch, dev, stream, timed, w, V,
+                                                   base["fp64_cgne_ms"] if base else None)
 
     # ---- aggregate over ranks ----------------------------------------------------------
     total_value = sum_over_ranks(dist, flops, dev) / (ms * 1e-3) / 1e9

@@ -17,6 +17,7 @@
 // gradient G = dL/dW^* = sum_x delta_c(x) (T_d a_{c'}(x))^+ (colour summed),
 // delta propagated backwards through the adjoint layers (W^+ and T_d^+ =
 // T_{opposite d}); Adam on the real and imaginary parts (gradient 2 Re G, 2 Im G).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -29,7 +30,6 @@
 namespace qxd {
 
 constexpr int kPtcMaxCh = 16;
-constexpr int kPtcThreads = 128;
 
 struct PtcLinks {
     const float4* U32;  // [p][12][Vh]
@@ -53,71 +53,136 @@ size_t ptc_weight_count(int nlayers, int nch) {
     return n;
 }
 
-// (T_d a)(x) for the site (p, h) with coordinates x: the source site and the link
-QXD_HD void transport(const Geo& g, const PtcLinks& L, int d, int p, int h, const int x[4],
-                      const float4* __restrict__ a_ch, cplx<float> t[12]) {
-    const int Vh = g.Vh;
-    if (d == 0) {
-        load_spinor<1>(a_ch + (size_t)p * 6 * Vh, Vh, h, t);
-        return;
-    }
-    const int mu = (d - 1) & 3;
-    const bool fwd = d <= 4;
-    const int src = neighbour_lex(g, x, mu, fwd ? +1 : -1) >> 1;
-    const int ps = 1 - p;
-    cplx<float> s[12];
-    load_spinor<1>(a_ch + (size_t)ps * 6 * Vh, Vh, src, s);
+// ---- transports --------------------------------------------------------------
+// Colour row I of (T_d a)(x), all four spins: t[s] = (T_d a)(x)[s][I].  The link
+// of direction d (and its phase) is loaded once per d by the caller (link_for);
+// `src` is the neighbour's half index (d > 0) on parity 1 - p.
+struct PtcLink {
     Mat3<float> m;
     cplx<float> z;
-    if (fwd) load_link32(L.U32 + (size_t)p * 12 * Vh, L.Z32 + (size_t)p * 2 * Vh, Vh, mu, h, m, z);
-    else load_link32(L.U32 + (size_t)ps * 12 * Vh, L.Z32 + (size_t)ps * 2 * Vh, Vh, mu, src, m, z);
-#pragma unroll
-    for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            cplx<float> acc = {0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (fwd) cmac(acc, m.a[i][j], s[3 * sp + j]);
-                else cmac_conj(acc, m.a[j][i], s[3 * sp + j]);
-            }
-            t[3 * sp + i] = fwd ? z * acc : cmul_conj(z, acc);
-        }
+    int src;
+};
+
+QXD_HD void link_for(const Geo& g, const PtcLinks& L, int d, int p, int h, const int x[4], PtcLink& lk) {
+    const int Vh = g.Vh;
+    const int mu = (d - 1) & 3;
+    const bool fwd = d <= 4;
+    lk.src = neighbour_lex(g, x, mu, fwd ? +1 : -1) >> 1;
+    const int ps = 1 - p;
+    if (fwd) load_link32(L.U32 + (size_t)p * 12 * Vh, L.Z32 + (size_t)p * 2 * Vh, Vh, mu, h, lk.m, lk.z);
+    else load_link32(L.U32 + (size_t)ps * 12 * Vh, L.Z32 + (size_t)ps * 2 * Vh, Vh, mu, lk.src, lk.m, lk.z);
 }
 
-// one thread per (site, output channel); grid (sites/threads, 2 parities, cout)
-__global__ void __launch_bounds__(kPtcThreads) k_ptc_layer(Geo g, PtcLinks L, const float4* __restrict__ a, int cin,
-                                                           const float2* __restrict__ W, float4* __restrict__ out) {
-    extern __shared__ float2 wsh[];  // this output channel's weights [cin][9][4][4]
-    const int c = blockIdx.z;
-    const int nw = cin * 9 * 16;
-    for (int i = threadIdx.x; i < nw; i += blockDim.x) wsh[i] = W[(size_t)c * nw + i];
-    __syncthreads();
-    const int p = blockIdx.y;
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= g.Vh) return;
+template <int I>
+QXD_HD void transport_row(const Geo& g, int d, int p, int h, const PtcLink& lk, const float4* __restrict__ a_ch,
+                          cplx<float> t[4]) {
+    const int Vh = g.Vh;
+    if (d == 0) {
+        const float4* b = a_ch + (size_t)p * 6 * Vh;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const int q = 3 * sp + I;
+            const float4 v = QXD_LDG(b + (size_t)(q >> 1) * Vh + h);
+            t[sp] = (q & 1) ? cplx<float>{v.z, v.w} : cplx<float>{v.x, v.y};
+        }
+        return;
+    }
+    cplx<float> s[12];
+    load_spinor<1>(a_ch + (size_t)(1 - p) * 6 * Vh, Vh, lk.src, s);
+    const bool fwd = d <= 4;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (fwd) cmac(acc, lk.m.a[I][j], s[3 * sp + j]);
+            else cmac_conj(acc, lk.m.a[j][I], s[3 * sp + j]);
+        }
+        t[sp] = fwd ? lk.z * acc : cmul_conj(lk.z, acc);
+    }
+}
+
+// ---- forward layer ------------------------------------------------------------------
+// Thread (site, colour I): a tile of kPtcSites sites of one parity, the three
+// colour rows in three groups of kPtcSites threads (warp-uniform colour).  Each
+// thread forms T_d a_{c'} once per (d, c') and accumulates all COUT output
+// channels of its group from it; the group's weights [9][cin][COUT][4][4] sit in
+// shared memory (read as broadcasts).  Persistent: a block loops over tiles.
+constexpr int kPtcSites = 64;
+constexpr int kPtcFwdThreads = 3 * kPtcSites;
+constexpr int kPtcGroup = 8;  // output channels per block (grid.z splits larger layers)
+
+template <int I, int COUT>
+__device__ void ptc_fwd_site(const Geo& g, const PtcLinks& L, const float4* __restrict__ a, int cin, int ng,
+                             const float2* __restrict__ wsh, float4* __restrict__ out, int c0, int p, int h) {
     const size_t chs = (size_t)12 * g.Vh;  // float4 per channel
     int x[4];
     site_coords(g, p, h, x);
-    cplx<float> acc[12];
+    cplx<float> acc[COUT][4];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+    for (int c = 0; c < COUT; ++c)
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) acc[c][sp] = {0.f, 0.f};
     for (int d = 0; d < 9; ++d) {
+        PtcLink lk;
+        if (d > 0) link_for(g, L, d, p, h, x, lk);
         for (int cp = 0; cp < cin; ++cp) {
-            cplx<float> t[12];
-            transport(g, L, d, p, h, x, a + cp * chs, t);
-            const float2* w = wsh + (cp * 9 + d) * 16;
+            cplx<float> t[4];
+            transport_row<I>(g, d, p, h, lk, a + cp * chs, t);
+            const float4* w = reinterpret_cast<const float4*>(wsh + (size_t)(d * cin + cp) * COUT * 16);
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+            for (int c = 0; c < COUT; ++c) {
+                if (c >= ng) break;
 #pragma unroll
                 for (int sp = 0; sp < 4; ++sp) {
-                    const cplx<float> wv = {w[4 * s + sp].x, w[4 * s + sp].y};
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) cmac(acc[3 * s + i], wv, t[3 * sp + i]);
+                    const float4 w01 = w[c * 8 + sp * 2], w23 = w[c * 8 + sp * 2 + 1];
+                    cmac(acc[c][sp], cplx<float>{w01.x, w01.y}, t[0]);
+                    cmac(acc[c][sp], cplx<float>{w01.z, w01.w}, t[1]);
+                    cmac(acc[c][sp], cplx<float>{w23.x, w23.y}, t[2]);
+                    cmac(acc[c][sp], cplx<float>{w23.z, w23.w}, t[3]);
                 }
+            }
         }
     }
-    store_spinor<1>(out + c * chs + (size_t)p * 6 * g.Vh, g.Vh, h, acc);
+    // complex (spin sp, colour I) is component (q & 1) of chunk q >> 1, q = 3 sp + I
+#pragma unroll
+    for (int c = 0; c < COUT; ++c) {
+        if (c >= ng) break;
+        float2* o = reinterpret_cast<float2*>(out + (c0 + c) * chs + (size_t)p * 6 * g.Vh);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const int q = 3 * sp + I;
+            o[2 * ((size_t)(q >> 1) * g.Vh + h) + (q & 1)] = make_float2(acc[c][sp].re, acc[c][sp].im);
+        }
+    }
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(kPtcFwdThreads) k_ptc_fwd(Geo g, PtcLinks L, const float4* __restrict__ a, int cin,
+                                                           int cout, const float2* __restrict__ W,
+                                                           float4* __restrict__ out) {
+    extern __shared__ float4 wsh4[];
+    float2* wsh = reinterpret_cast<float2*>(wsh4);
+    const int c0 = blockIdx.z * kPtcGroup;
+    const int ng = min(kPtcGroup, cout - c0);
+    // W[c][c'][d][s][s'] (global) -> wsh[d][c'][c - c0][s][s'] (zero for c >= ng)
+    const int nw = 9 * cin * COUT * 16;
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) {
+        const int e = i % 16, c = (i / 16) % COUT, cp = (i / (16 * COUT)) % cin, d = i / (16 * COUT * cin);
+        wsh[i] = c < ng ? W[((size_t)((c0 + c) * cin + cp) * 9 + d) * 16 + e] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int colour = threadIdx.x / kPtcSites;
+    const int lane_site = threadIdx.x % kPtcSites;
+    const int tiles = (g.Vh + kPtcSites - 1) / kPtcSites;
+    for (int t = blockIdx.x; t < 2 * tiles; t += gridDim.x) {
+        const int p = t / tiles;
+        const int h = (t % tiles) * kPtcSites + lane_site;
+        if (h >= g.Vh) continue;
+        if (colour == 0) ptc_fwd_site<0, COUT>(g, L, a, cin, ng, wsh, out, c0, p, h);
+        else if (colour == 1) ptc_fwd_site<1, COUT>(g, L, a, cin, ng, wsh, out, c0, p, h);
+        else ptc_fwd_site<2, COUT>(g, L, a, cin, ng, wsh, out, c0, p, h);
+    }
 }
 
 // W'[c'][c][d'] = W[c][c'][opposite(d')]^+ (the adjoint layer as a forward layer)
@@ -133,81 +198,131 @@ __global__ void k_ptc_adjoint_weights(const float2* __restrict__ W, int cin, int
     }
 }
 
-// partial weight gradients: block (site chunk, triple q = (c*cin + c')*9 + d)
-constexpr int kWgBlocks = 32;
-__global__ void __launch_bounds__(kPtcThreads) k_ptc_wgrad(Geo g, PtcLinks L, const float4* __restrict__ delta,
-                                                           const float4* __restrict__ a, int cin,
-                                                           double* __restrict__ partials) {
-    const int q = blockIdx.y;
-    const int d = q % 9, cp = (q / 9) % cin, c = q / (9 * cin);
+// ---- weight gradient ----------------------------------------------------------------
+// G[c][c'][d][s][s'] = sum_{x,i} delta_c(x)[s][i] conj((T_d a_{c'})(x)[s'][i]): for each d
+// the product of the (c,s) x (x,i) matrix of delta with the (x,i) x (c',s') matrix of
+// conjugated transports, summed over K = 3V rows in tiles of 3 kPtcSites rows.  A block
+// owns one chunk (blockIdx.z) of at most 32 (c,s) x 32 (c',s') entries for all nine d;
+// each of its 256 threads a 2 x 2 sub-block of the chunk for every d (36 complex
+// accumulators).  Per tile the delta rows are staged once and the transports once per
+// d, both in shared memory; T_d a_{c'} is formed once per site, colour, d and c'.
+// Sums run in FP32 within a block; the blocks' partials are added in FP64 in a fixed
+// order by k_ptc_wgrad_final.
+constexpr int kWgThreads = 256;
+constexpr int kWgRows = 3 * kPtcSites;
+constexpr size_t kWgSmem = 2ull * kWgRows * 32 * sizeof(float2);  // delta and transport tiles
+
+template <int I>
+__device__ void wgrad_stage(const Geo& g, const PtcLinks& L, const float4* __restrict__ delta,
+                            const float4* __restrict__ a, int d, int p, int h, bool live, int r_c0, int nr_c,
+                            int c_c0, int nc_c, float2 (*dsh)[32], float2 (*tsh)[32], int row) {
     const size_t chs = (size_t)12 * g.Vh;
-    float f[32];
-    double acc[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        f[k] = 0.f;
-        acc[k] = 0.0;
-    }
-    int cnt = 0;
-    const int nsite = 2 * g.Vh;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nsite; t += gridDim.x * blockDim.x) {
-        const int p = t / g.Vh, h = t % g.Vh;
-        int x[4];
-        site_coords(g, p, h, x);
-        cplx<float> s[12], dl[12];
-        transport(g, L, d, p, h, x, a + cp * chs, s);
-        load_spinor<1>(delta + c * chs + (size_t)p * 6 * g.Vh, g.Vh, h, dl);
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                cplx<float> v = {0.f, 0.f};
-#pragma unroll
-                for (int col = 0; col < 3; ++col) cmac_conj(v, s[3 * j + col], dl[3 * i + col]);
-                // v = sum_col conj(s[j][col]) delta[i][col] = (delta s^+)_{ij}
-                f[2 * (4 * i + j)] += v.re;
-                f[2 * (4 * i + j) + 1] += v.im;
+    int x[4];
+    if (live) site_coords(g, p, h, x);
+    if (d < 0) {
+        // delta_c(x)[s][I] for the chunk's output channels
+        for (int c = 0; c < 8; ++c) {
+            cplx<float> t[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            if (live && c < nr_c) {
+                PtcLink none;
+                transport_row<I>(g, 0, p, h, none, delta + (r_c0 + c) * chs, t);
             }
-        if (++cnt == 16) {
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                acc[k] += f[k];
-                f[k] = 0.f;
-            }
-            cnt = 0;
+            for (int sp = 0; sp < 4; ++sp) dsh[row][c * 4 + sp] = make_float2(t[sp].re, t[sp].im);
         }
+        return;
     }
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] += f[k];
-    __shared__ double sh[32][kPtcThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[k][warp] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = 0.0;
-        for (int w = 0; w < kPtcThreads / 32; ++w) v += sh[threadIdx.x][w];
-        partials[((size_t)q * gridDim.x + blockIdx.x) * 32 + threadIdx.x] = v;
+    PtcLink lk;
+    if (live && d > 0) link_for(g, L, d, p, h, x, lk);
+    for (int c = 0; c < 8; ++c) {
+        cplx<float> t[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+        if (live && c < nc_c) transport_row<I>(g, d, p, h, lk, a + (c_c0 + c) * chs, t);
+        for (int sp = 0; sp < 4; ++sp) tsh[row][c * 4 + sp] = make_float2(t[sp].re, t[sp].im);
     }
 }
 
-// G[q] (+)= sum over blocks of partials, fixed order; complex float output
-__global__ void k_ptc_wgrad_final(const double* __restrict__ partials, int nq, int nb, float2* __restrict__ G,
-                                  int accumulate) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nq * 16; t += gridDim.x * blockDim.x) {
-        const int q = t / 16, e = t % 16;
-        double re = 0.0, im = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            re += partials[((size_t)q * nb + b) * 32 + 2 * e];
-            im += partials[((size_t)q * nb + b) * 32 + 2 * e + 1];
+__global__ void __launch_bounds__(kWgThreads) k_ptc_wgrad(Geo g, PtcLinks L, const float4* __restrict__ delta,
+                                                         const float4* __restrict__ a, int cin, int cout,
+                                                         float2* __restrict__ partials) {
+    extern __shared__ float4 wg_sh[];
+    float2 (*dsh)[32] = reinterpret_cast<float2 (*)[32]>(wg_sh);
+    float2 (*tsh)[32] = dsh + kWgRows;
+    const int nzc = (cin + 7) / 8;
+    const int zr = blockIdx.z / nzc, zc = blockIdx.z % nzc;
+    const int r_c0 = 8 * zr, nr_c = min(8, cout - r_c0);  // output channels of the chunk
+    const int c_c0 = 8 * zc, nc_c = min(8, cin - c_c0);   // input channels of the chunk
+    const int tid = threadIdx.x;
+    const int r0 = 2 * (tid / 16), q0 = 2 * (tid % 16);  // this thread's 2 x 2 sub-block
+    cplx<float> acc[9][2][2];
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) acc[d][i][j] = {0.f, 0.f};
+    const int colour = tid / kPtcSites;  // staging threads: tid < kWgRows
+    const int lane_site = tid % kPtcSites;
+    const int tiles = (g.Vh + kPtcSites - 1) / kPtcSites;
+    for (int t = blockIdx.x; t < 2 * tiles; t += gridDim.x) {
+        const int p = t / tiles;
+        const int h = (t % tiles) * kPtcSites + lane_site;
+        const bool live = h < g.Vh;
+        __syncthreads();  // the previous tile's rows are no longer read
+        if (tid < kWgRows) {
+            if (colour == 0) wgrad_stage<0>(g, L, delta, a, -1, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
+            else if (colour == 1) wgrad_stage<1>(g, L, delta, a, -1, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
+            else wgrad_stage<2>(g, L, delta, a, -1, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
         }
-        float2 g0 = accumulate ? G[t] : make_float2(0.f, 0.f);
-        G[t] = make_float2(g0.x + (float)re, g0.y + (float)im);
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+            __syncthreads();
+            if (tid < kWgRows) {
+                if (colour == 0) wgrad_stage<0>(g, L, delta, a, d, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
+                else if (colour == 1) wgrad_stage<1>(g, L, delta, a, d, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
+                else wgrad_stage<2>(g, L, delta, a, d, p, h, live, r_c0, nr_c, c_c0, nc_c, dsh, tsh, tid);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int k = 0; k < kWgRows; ++k) {
+                const float4 dv = *reinterpret_cast<const float4*>(&dsh[k][r0]);
+                const float4 tv = *reinterpret_cast<const float4*>(&tsh[k][q0]);
+                const cplx<float> dd[2] = {{dv.x, dv.y}, {dv.z, dv.w}};
+                const cplx<float> tt[2] = {{tv.x, tv.y}, {tv.z, tv.w}};
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) cmac_conj(acc[d][i][j], tt[j], dd[i]);
+            }
+        }
+    }
+    float2* out = partials + ((size_t)blockIdx.z * gridDim.x + blockIdx.x) * 9 * 1024;
+#pragma unroll
+    for (int d = 0; d < 9; ++d)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                out[d * 1024 + (r0 + i) * 32 + (q0 + j)] = make_float2(acc[d][i][j].re, acc[d][i][j].im);
+}
+
+// G (+)= sum over the blocks' partials in FP64, blocks in a fixed order
+__global__ void k_ptc_wgrad_final(const float2* __restrict__ partials, int nblk, int cin, int cout,
+                                  float2* __restrict__ G, int accumulate) {
+    const int nzc = (cin + 7) / 8, nz = ((cout + 7) / 8) * nzc;
+    const int n = nz * 9 * 1024;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        const int e = t % 1024, d = (t / 1024) % 9, z = t / (9 * 1024);
+        const int r = e / 32, q = e % 32;
+        const int c = 8 * (z / nzc) + r / 4, cp = 8 * (z % nzc) + q / 4;
+        if (c >= cout || cp >= cin) continue;
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            const float2 v = partials[((size_t)z * nblk + b) * 9 * 1024 + d * 1024 + e];
+            re += v.x;
+            im += v.y;
+        }
+        const size_t o = ((size_t)(c * cin + cp) * 9 + d) * 16 + (r % 4) * 4 + (q % 4);
+        const float2 g0 = accumulate ? G[o] : make_float2(0.f, 0.f);
+        G[o] = make_float2(g0.x + (float)re, g0.y + (float)im);
     }
 }
 
@@ -229,13 +344,61 @@ static PtcLinks links_of(qxd_ctx* ctx, int fl) { return PtcLinks{ctx->U32, ctx->
 
 static size_t chan_bytes(const qxd_ctx* ctx) { return (size_t)ctx->g.Vh * 2 * 96; }
 
+// one forward layer: COUT = output channels per block (the smallest of 1, 2, 4, 8 that
+// holds min(cout, 8)), grid.z = groups of 8 output channels, a persistent grid of
+// resident blocks over the tiles of both parities
+template <int COUT>
+static int launch_fwd(qxd_ctx* ctx, int fl, const float4* a, int cin, const float2* W, float4* out, int cout,
+                      cudaStream_t st) {
+    const Geo& g = ctx->g;
+    const size_t smem = 9ull * cin * COUT * 16 * sizeof(float2);
+    QXD_CUDA(ctx, cudaFuncSetAttribute(k_ptc_fwd<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    QXD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ptc_fwd<COUT>, kPtcFwdThreads, smem));
+    const int groups = (cout + kPtcGroup - 1) / kPtcGroup;
+    const int tiles = 2 * ((g.Vh + kPtcSites - 1) / kPtcSites);
+    const int nx = std::max(1, std::min(tiles, std::max(1, per_sm) * ctx->nsm / groups));
+    k_ptc_fwd<COUT><<<dim3(nx, 1, groups), kPtcFwdThreads, smem, st>>>(g, links_of(ctx, fl), a, cin, cout, W, out);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+// algorithmic bytes of a layer: every input and output channel once, the links once
+static double layer_bytes(const qxd_ctx* ctx, int cin, int cout) {
+    return (double)chan_bytes(ctx) * (cin + cout) + (double)ctx->g.V * 4 * 56;
+}
+
 static int launch_layer(qxd_ctx* ctx, int fl, const float4* a, int cin, const float2* W, float4* out, int cout,
                         cudaStream_t st) {
+    ProfScope prof(ctx, "ptc_layer", layer_bytes(ctx, cin, cout), st);
+    const int cg = std::min(cout, kPtcGroup);
+    if (cg <= 1) return launch_fwd<1>(ctx, fl, a, cin, W, out, cout, st);
+    if (cg <= 2) return launch_fwd<2>(ctx, fl, a, cin, W, out, cout, st);
+    if (cg <= 4) return launch_fwd<4>(ctx, fl, a, cin, W, out, cout, st);
+    return launch_fwd<8>(ctx, fl, a, cin, W, out, cout, st);
+}
+
+// weight gradient of one layer into G (accumulated): grid (blocks, 1, chunks)
+static int wgrad_blocks(const qxd_ctx* ctx) {
+    const int tiles = 2 * ((ctx->g.Vh + kPtcSites - 1) / kPtcSites);
+    return std::max(1, std::min(tiles, 2 * ctx->nsm));
+}
+
+static size_t wgrad_partial_bytes(const qxd_ctx* ctx, int cin, int cout) {
+    const size_t nz = (size_t)((cout + 7) / 8) * ((cin + 7) / 8);
+    return nz * wgrad_blocks(ctx) * 9 * 1024 * sizeof(float2);
+}
+
+static int launch_wgrad(qxd_ctx* ctx, int fl, const float4* delta, const float4* a, int cin, int cout, float2* part,
+                        float2* G, cudaStream_t st) {
     const Geo& g = ctx->g;
-    dim3 grid(nblocks(g.Vh, kPtcThreads), 2, cout);
-    const size_t smem = (size_t)cin * 9 * 16 * sizeof(float2);
-    ProfScope prof(ctx, "ptc_layer", (double)chan_bytes(ctx) * (cin * 9 + cout) + 2.0 * g.Vh * 4 * 56, st);
-    k_ptc_layer<<<grid, kPtcThreads, smem, st>>>(g, links_of(ctx, fl), a, cin, W, out);
+    ProfScope prof(ctx, "ptc_wgrad", layer_bytes(ctx, cin, cout), st);
+    QXD_CUDA(ctx, cudaFuncSetAttribute(k_ptc_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem));
+    const int nblk = wgrad_blocks(ctx);
+    const int nz = ((cout + 7) / 8) * ((cin + 7) / 8);
+    k_ptc_wgrad<<<dim3(nblk, 1, nz), kWgThreads, kWgSmem, st>>>(g, links_of(ctx, fl), delta, a, cin, cout, part);
+    QXD_CUDA(ctx, cudaGetLastError());
+    k_ptc_wgrad_final<<<nblocks((long long)nz * 9 * 1024, 256), 256, 0, st>>>(part, nblk, cin, cout, G, 1);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }
@@ -298,7 +461,7 @@ static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nla
     QXD_TRY(qxd_ws(ctx, WS_PTC + 10, chan_bytes(ctx) * nch, &dA));
     QXD_TRY(qxd_ws(ctx, WS_PTC + 11, chan_bytes(ctx) * nch, &dB));
     QXD_TRY(qxd_ws(ctx, WS_PTC + 12, layer_weights(nch, nch) * sizeof(float2), &Wa));
-    QXD_TRY(qxd_ws(ctx, WS_PTC + 13, (size_t)nch * nch * 9 * kWgBlocks * 32 * sizeof(double), &part));
+    QXD_TRY(qxd_ws(ctx, WS_PTC + 13, wgrad_partial_bytes(ctx, nch, nch), &part));
     // offsets of each layer's weights
     std::vector<size_t> off(nlayers + 1, 0);
     for (int l = 0; l < nlayers; ++l) {
@@ -329,16 +492,7 @@ static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nla
             int ci, co;
             layer_shape(l, nlayers, nch, &ci, &co);
             const int nq = co * ci * 9;
-            {
-                ProfScope prof(ctx, "ptc_wgrad", (double)chan_bytes(ctx) * (ci + co) * 9, st);
-                dim3 grid(kWgBlocks, nq);
-                k_ptc_wgrad<<<grid, kPtcThreads, 0, st>>>(g, links_of(ctx, fl), dcur, acts[l], ci,
-                                                          static_cast<double*>(part));
-                QXD_CUDA(ctx, cudaGetLastError());
-                k_ptc_wgrad_final<<<nblocks(nq * 16, 256), 256, 0, st>>>(static_cast<double*>(part), nq, kWgBlocks,
-                                                                       G + off[l], 1);
-                QXD_CUDA(ctx, cudaGetLastError());
-            }
+            QXD_TRY(launch_wgrad(ctx, fl, dcur, acts[l], ci, co, static_cast<float2*>(part), G + off[l], st));
             if (l > 0) {
                 k_ptc_adjoint_weights<<<nblocks(nq, 128), 128, 0, st>>>(W + off[l], ci, co,
                                                                         static_cast<float2*>(Wa));

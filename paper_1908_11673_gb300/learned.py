@@ -43,32 +43,87 @@ def identity_weights(nlayers, nch):
 
 
 def make_context(seed, device=0, field=FIELD):
-    U, A = workload.gauge_field(field["L"], seed, stout_steps=field["stout"], rho=field["rho"])
+    U, A = workload.gauge_field(field["L"], seed, stout_steps=field["stout"], rho=field["rho"],
+                                u1_stout_steps=field.get("u1_stout", 0))
     ctx = qxd.Context(field["L"], field["cstar"], field["theta"], device=device)
     ctx.set_links(U, A, field["invqel"])
     ctx.set_clover(0, field["qhat"], field["kappa"], field["su3csw"], field["u1csw"])
     return ctx
 
 
-def record(ctx, seed, npairs):
-    """npairs pairs spread over one plain FP64 solve of Dhat x = b (b Gaussian)."""
+def record(ctx, seed, npairs, stride=None):
+    """npairs pairs spread over one plain FP64 solve of Dhat x = b (b Gaussian):
+    every `stride`-th iterate, or (stride None) the largest stride for which the
+    solve has npairs * stride iterations (found by bisection)."""
     ne = ctx.Vh
     b = workload.spinor(ne, seed)
-    # count the iterations of the plain solve first, then sample its iterates evenly
-    probe_r = np.empty((1, ne, 4, 3), dtype=np.complex64)
-    probe_e = np.empty_like(probe_r)
-    lo, hi = 1, 4096
-    while lo < hi:  # largest stride s with npairs * s iterations available
-        mid = (lo + hi + 1) // 2
-        try:
-            ctx.ptc_record_pairs(0, b, 1, mid * npairs, probe_r, probe_e)
-            lo = mid
-        except qxd.QxdError:
-            hi = mid - 1
+    lo = stride
+    if lo is None:
+        # count the iterations of the plain solve first, then sample its iterates evenly
+        probe_r = np.empty((1, ne, 4, 3), dtype=np.complex64)
+        probe_e = np.empty_like(probe_r)
+        lo, hi = 1, 4096
+        while lo < hi:  # largest stride s with npairs * s iterations available
+            mid = (lo + hi + 1) // 2
+            try:
+                ctx.ptc_record_pairs(0, b, 1, mid * npairs, probe_r, probe_e)
+                lo = mid
+            except qxd.QxdError:
+                hi = mid - 1
     r = np.empty((npairs, ne, 4, 3), dtype=np.complex64)
     e = np.empty_like(r)
     ctx.ptc_record_pairs(0, b, npairs, lo, r, e)
     return r, e, lo
+
+
+def train(field, seeds, npairs, epochs=6, batch=10, lr=2e-3, nlayers=4, nch=8, stride=None, device=0):
+    """Train the network on pairs recorded on the fields of `seeds` (one context
+    per field, all on the GPU): Adam from the identity network, `epochs` passes
+    over every field's pairs in batches.  Returns (W, summary) with the mean loss
+    per epoch and the mean loss of the identity, the zero map (1 by definition)
+    and the trained network over all pairs."""
+    t0 = time.time()
+    W = identity_weights(nlayers, nch)
+    m = np.zeros_like(W)
+    v = np.zeros_like(W)
+    t = np.zeros(1, dtype=np.int32)
+    data = []
+    for i, sd in enumerate(seeds):
+        ctx = make_context(sd, device, field)
+        r, e, st = record(ctx, 10 * sd + 1, npairs, stride)
+        data.append((ctx, r, e))
+    t_pairs = time.time() - t0
+    history = []
+    steps = max(1, npairs // batch)
+    for _ in range(epochs):
+        el = []
+        for ctx, r, e in data:
+            el.extend(ctx.ptc_train(0, W, m, v, nlayers, nch, r, e, npairs, batch, steps, lr, t).tolist())
+        history.append(float(np.mean(el)))
+    t_train = time.time() - t0 - t_pairs
+    ident = identity_weights(nlayers, nch)
+    loss_id = float(np.mean([ctx.ptc_loss_grad(0, ident, nlayers, nch, r, e, npairs) / npairs
+                             for ctx, r, e in data]))
+    loss_tr = float(np.mean([ctx.ptc_loss_grad(0, W, nlayers, nch, r, e, npairs) / npairs for ctx, r, e in data]))
+    for ctx, _, _ in data:
+        ctx.close()
+    return W, {"fields": len(seeds), "pairs": len(seeds) * npairs, "network": f"{nlayers} layers x {nch} channels",
+               "epochs": epochs, "loss_zero_map": 1.0, "loss_identity": loss_id, "loss_trained": loss_tr,
+               "loss_history": history, "seconds_pairs": t_pairs, "seconds_training": t_train}
+
+
+def residual_reduction(ctx, W, nlayers, nch, r):
+    """Mean of |r - Dhat M r|^2 / |r|^2 over the residuals r [n][V/2][4][3]
+    (complex64): how much of r one application of M Dhat removes (1 for M = 0),
+    through qxd_ptc_apply and qxd_apply_Dhat_eo (FP32)."""
+    out = []
+    Mr = np.empty_like(r[0])
+    DMr = np.empty_like(r[0])
+    for ri in r:
+        ctx.ptc_apply(0, W, nlayers, nch, ri, Mr)
+        ctx.apply_Dhat_eo(0, qxd.FP32, Mr, DMr)
+        out.append(float(np.linalg.norm(ri - DMr) ** 2 / np.linalg.norm(ri) ** 2))
+    return float(np.mean(out))
 
 
 def evaluate(ctx, W, nlayers, nch, seed, nkv=16):
@@ -106,33 +161,8 @@ def main(argv=None):
     ap.add_argument("--weights", default=None, help="save the trained weights (.npy)")
     args = ap.parse_args(argv)
 
-    t0 = time.time()
-    W = identity_weights(args.nlayers, args.nch)
-    m = np.zeros_like(W)
-    v = np.zeros_like(W)
-    t = np.zeros(1, dtype=np.int32)
-    data = []
-    for i in range(args.train_fields):
-        ctx = make_context(4000 + i)
-        r, e, stride = record(ctx, 40000 + i, args.pairs)
-        data.append((ctx, r, e))
-    t_pairs = time.time() - t0
-    history = []
-    steps = max(1, args.pairs // args.batch)
-    for ep in range(args.epochs):
-        el = []
-        for ctx, r, e in data:
-            el.extend(ctx.ptc_train(0, W, m, v, args.nlayers, args.nch, r, e, args.pairs, args.batch, steps,
-                                    args.lr, t).tolist())
-        history.append(float(np.mean(el)))
-    t_train = time.time() - t0 - t_pairs
-    base_loss = float(np.mean([ctx.ptc_loss_grad(0, identity_weights(args.nlayers, args.nch), args.nlayers, args.nch,
-                                                 r, e, args.pairs)
-                               / args.pairs for ctx, r, e in data]))
-    final_loss = float(np.mean([ctx.ptc_loss_grad(0, W, args.nlayers, args.nch, r, e, args.pairs) / args.pairs
-                                for ctx, r, e in data]))
-    for ctx, _, _ in data:
-        ctx.close()
+    W, summ_train = train(FIELD, [4000 + i for i in range(args.train_fields)], args.pairs, args.epochs, args.batch,
+                          args.lr, args.nlayers, args.nch)
     evals = []
     for i in range(args.eval_fields):
         ctx = make_context(4100 + i)
@@ -141,11 +171,7 @@ def main(argv=None):
     summ = {k: {"iters_mean": float(np.mean([e[k]["iters"] for e in evals])),
                 "ms_mean": float(np.mean([e[k]["ms"] for e in evals])),
                 "max_true_relres": float(max(e[k]["true_relres"] for e in evals))} for k in evals[0]}
-    result = {"train_fields": args.train_fields, "pairs": args.train_fields * args.pairs,
-              "network": f"{args.nlayers} layers x {args.nch} channels", "epochs": args.epochs,
-              "loss_identity": base_loss, "loss_trained": final_loss, "loss_history": history,
-              "seconds_pairs": t_pairs, "seconds_training": t_train, "eval_fields": args.eval_fields,
-              "held_out": summ}
+    result = summ_train | {"eval_fields": args.eval_fields, "held_out": summ}
     print(json.dumps(result, indent=1))
     if args.out:
         with open(args.out, "w") as f:

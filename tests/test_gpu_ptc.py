@@ -36,26 +36,30 @@ def unflat(x, nlayers, nch):
 GEOMS = [((4, 4, 4, 6), 0, (np.pi, 0, 0, 0)), ((4, 4, 6, 4), 2, (np.pi, 0, 0, 0))]
 
 
+# channel counts: 4 and 3 fit one block's output group, 12 takes two groups of
+# the forward kernel and four chunks of the weight-gradient kernel
 @pytest.mark.parametrize("L,cstar,theta", GEOMS)
-def test_forward_parity(L, cstar, theta):
+@pytest.mark.parametrize("nch", [4, 12])
+def test_forward_parity(L, cstar, theta, nch):
     qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=4, seed=7100)
-    Ws = rand_weights(np.random.default_rng(1), 4, 4)
+    Ws = rand_weights(np.random.default_rng(1), 4, nch)
     ne = op.geom.V // 2
     r = workload.spinor(ne, 7101).astype(np.complex64)
     out = np.empty_like(r)
-    ctx.ptc_apply(0, flat(Ws), 4, 4, r, out)
+    ctx.ptc_apply(0, flat(Ws), 4, nch, r, out)
     ref = ptc.network(ptc.Transport(op), Ws, r.astype(np.complex128))
     assert relerr(out.astype(np.complex128), ref) <= 1e-5
     ident = np.empty_like(r)
-    ctx.ptc_apply(0, flat(ptc.identity_weights(4, 4)), 4, 4, r, ident)
+    ctx.ptc_apply(0, flat(ptc.identity_weights(4, nch)), 4, nch, r, ident)
     assert np.array_equal(ident, r)
     ctx.close()
 
 
 @pytest.mark.parametrize("L,cstar,theta", GEOMS)
-def test_loss_and_gradient_parity(L, cstar, theta):
+@pytest.mark.parametrize("nch", [3, 12])
+def test_loss_and_gradient_parity(L, cstar, theta, nch):
     qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=-2, seed=7200)
-    nl, nch = 3, 3
+    nl = 3
     Ws = rand_weights(np.random.default_rng(2), nl, nch)
     ne = op.geom.V // 2
     r = workload.spinor(ne, 7201, nrhs=2).astype(np.complex64)
@@ -102,4 +106,60 @@ def test_training_reduces_loss_and_fgcr_uses_the_network():
     sites = np.random.default_rng(0).choice(op.geom.V, 1000, replace=False)
     res = eta[sites] - op.apply(psi, sites)
     assert np.linalg.norm(res) / np.linalg.norm(eta[sites]) < 1e-9
+    ctx.close()
+
+
+def test_learned_preconditioner_gain_16x16x16x16():
+    """What the trained network gains over the method without it, on the 16^4
+    configuration (5 stout steps, qhat = -2, kappa = 0.136377, csw 1.90952/1.0).
+    Training: 4 layers x 8 channels from the identity, Adam on 4 x 50 pairs
+    recorded from the plain FP64 solver on fields 4000..4003.  Held-out field
+    4100: FGCR(16) with FP32 inner solves to the true FP64 residual 1e-10, with
+    and without the network as right preconditioner; the network must cut both
+    the iterations and the device time, and both solutions pass the oracle's
+    residual check.  Reported beside them: the training loss against the zero map
+    (loss 1 by definition) and the identity, and the share of a held-out residual
+    that one application of Dhat M leaves (1 for M = 0)."""
+    import torch
+
+    from paper_1908_11673_gb300 import learned
+    from tests.gpu_helpers import need_gpu
+    qxd = need_gpu()
+    nl, nch = 4, 8
+    W, summ = learned.train(learned.FIELD, [4000, 4001, 4002, 4003], 50, epochs=4, batch=10)
+    print("training:", summ, flush=True)
+    assert summ["loss_trained"] < summ["loss_identity"] and summ["loss_trained"] < summ["loss_zero_map"]
+    f = learned.FIELD
+    U, A = workload.gauge_field(f["L"], 4100, stout_steps=f["stout"], rho=f["rho"])
+    from oracle import DiracOperator, Flavour, GaugeField, Geometry
+    op = DiracOperator(GaugeField(Geometry(f["L"], 0, f["theta"]), U, A, f["invqel"]),
+                       Flavour(f["qhat"], f["kappa"], f["su3csw"], f["u1csw"]))
+    ctx = qxd.Context(f["L"], 0, f["theta"])
+    ctx.set_links(U, A, f["invqel"])
+    ctx.set_clover(0, f["qhat"], f["kappa"], f["su3csw"], f["u1csw"])
+    r_held, _, _ = learned.record(ctx, 41001, 8, stride=4)
+    red = learned.residual_reduction(ctx, W, nl, nch, r_held)
+    red_id = learned.residual_reduction(ctx, learned.identity_weights(nl, nch), nl, nch, r_held)
+    print(f"held-out |r - Dhat M r|^2/|r|^2: trained {red:.4f}, identity {red_id:.4f}, zero map 1", flush=True)
+    assert red < 1.0
+    ctx.set_precond_weights(0, W, nl, nch)
+    eta = workload.spinor(op.geom.V, 41000)
+    res = {}
+    for name, pre in (("none", qxd.PRECOND_NONE), ("learned", qxd.PRECOND_LEARNED)):
+        psi = np.empty_like(eta)
+        ctx.solve(0, eta, psi, kind=qxd.FGCR, tol=1e-10, inner=qxd.FP32, nkv=16, precond=pre)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = ctx.solve(0, eta, psi, kind=qxd.FGCR, tol=1e-10, inner=qxd.FP32, nkv=16, precond=pre)
+        e1.record()
+        torch.cuda.synchronize()
+        assert info.status == 0 and info.true_relres <= 1e-10, info.asdict()
+        rel = float(np.linalg.norm(eta - op.apply(psi)) / np.linalg.norm(eta))
+        assert rel <= 1.5e-10, (name, rel)
+        res[name] = (info.iters, e0.elapsed_time(e1), rel)
+    print(f"held-out FGCR to 1e-10: without M {res['none'][0]} iterations {res['none'][1]:.1f} ms, "
+          f"with M {res['learned'][0]} iterations {res['learned'][1]:.1f} ms", flush=True)
+    assert res["learned"][0] < res["none"][0]
+    assert res["learned"][1] < res["none"][1]
     ctx.close()
