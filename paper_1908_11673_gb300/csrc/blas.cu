@@ -684,6 +684,75 @@ __global__ void __launch_bounds__(kRedThreads) k_multi_axpy(size_t nch, MultiPtr
     }
 }
 
+// One GCR step's update in one pass (same precision): w += sum_j c_j X_j, then
+// z = x + a w with the updated w (the residual update r_{k+1} = r_k - alpha w_k').
+template <int P, int K>
+__global__ void k_gcr_update(size_t nch, MultiPtr X, MultiCoef c, void* __restrict__ w, double ar, double ai,
+                             const void* __restrict__ x, void* __restrict__ z) {
+    using R = typename Chunk<P>::R;
+    constexpr int NC = Chunk<P>::NC;
+    cplx<R> cf[K > 0 ? K : 1];
+#pragma unroll
+    for (int j = 0; j < K; ++j) cf[j] = {(R)c.re[j], (R)c.im[j]};
+    const cplx<R> a = {(R)ar, (R)ai};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nch; i += (size_t)gridDim.x * blockDim.x) {
+        cplx<R> wv[NC], xv[NC];
+        Chunk<P>::ld(w, i, wv);
+        Chunk<P>::ld(x, i, xv);
+        if constexpr (K > 0) {
+            cplx<R> yv[K][NC];
+#pragma unroll
+            for (int j = 0; j < K; ++j) Chunk<P>::ld(X.p[j], i, yv[j]);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int q = 0; q < NC; ++q) cmac(wv[q], cf[j], yv[j][q]);
+            Chunk<P>::st(w, i, wv);
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) cmac(xv[q], a, wv[q]);
+        Chunk<P>::st(z, i, xv);
+    }
+}
+
+template <int P>
+static void gcr_update_k(qxd_ctx* ctx, int k, size_t nch, const MultiPtr& X, const MultiCoef& c, void* w, double ar,
+                         double ai, const void* x, void* z, cudaStream_t st) {
+    const int nb = upd_blocks(ctx, nch);
+#define QXD_GU(K) k_gcr_update<P, K><<<nb, 256, 0, st>>>(nch, X, c, w, ar, ai, x, z)
+    switch (k) {
+        case 0: QXD_GU(0); break;
+        case 1: QXD_GU(1); break;
+        case 2: QXD_GU(2); break;
+        case 3: QXD_GU(3); break;
+        case 4: QXD_GU(4); break;
+        case 5: QXD_GU(5); break;
+        case 6: QXD_GU(6); break;
+        case 7: QXD_GU(7); break;
+        default: QXD_GU(8); break;
+    }
+#undef QXD_GU
+}
+
+int blas_gcr_update(qxd_ctx* ctx, int p, size_t n, int k, const double* cre, const double* cim,
+                    const void* const* X, void* w, double ar, double ai, const void* x, void* z, cudaStream_t st) {
+    if (k > kMultiMax) return qxd_fail(ctx, QXD_EARG, "blas_gcr_update: at most 8 basis vectors");
+    MultiPtr mp;
+    MultiCoef mc;
+    for (int j = 0; j < kMultiMax; ++j) {
+        mp.p[j] = j < k ? X[j] : w;
+        mc.re[j] = j < k ? cre[j] : 0.0;
+        mc.im[j] = j < k ? cim[j] : 0.0;
+    }
+    ProfScope prof(ctx, "gcr_update", (double)n * eb(p) * (k + (k > 0 ? 4 : 3)), st);
+    const size_t nc = nchunks(p, n);
+    if (p == 0) gcr_update_k<0>(ctx, k, nc, mp, mc, w, ar, ai, x, z, st);
+    else if (p == 1) gcr_update_k<1>(ctx, k, nc, mp, mc, w, ar, ai, x, z, st);
+    else gcr_update_k<2>(ctx, k, nc, mp, mc, w, ar, ai, x, z, st);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
 int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, const void* x, double br, double bi,
                void* y, cudaStream_t st) {
     const bool rb = !(br == 0.0 && bi == 0.0);

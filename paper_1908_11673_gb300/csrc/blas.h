@@ -51,6 +51,10 @@ int blas_multi_dot(qxd_ctx* ctx, int p, size_t n, int k, const void* const* W, c
 int blas_axpby(qxd_ctx* ctx, int px, int py, size_t n, double ar, double ai, const void* x, double br, double bi,
                void* y, cudaStream_t st);
 // z = x + a w (same precision, out of place)
+// GCR step in one pass: w += sum_{j<k} (cre_j + i cim_j) X_j, then z = x + (ar + i ai) w
+// (same precision P, k <= 8; z may not alias w or the X_j)
+int blas_gcr_update(qxd_ctx* ctx, int p, size_t n, int k, const double* cre, const double* cim,
+                    const void* const* X, void* w, double ar, double ai, const void* x, void* z, cudaStream_t st);
 int blas_axpy3(qxd_ctx* ctx, int p, size_t n, double ar, double ai, const void* w, const void* x, void* z,
                cudaStream_t st);
 // y += sum_j c_j X_j  (px == py)

@@ -6,6 +6,7 @@
 // (C* shifted boundaries included); (1 -+ gamma_mu) are applied as spin
 // projections onto two-spinors before the colour multiplication.
 #include <cstdio>
+#include <tuple>
 
 #include "hop.cuh"
 #include "qxd_internal.h"
@@ -17,8 +18,10 @@ static double spinor_bytes(int P) { return (P == 0 || P == 3) ? 192.0 : (P == 1 
 static double link_bytes(int P) { return (P == 0 || P == 3) ? 144.0 : 56.0; }   // V (FP64) or 2 rows of U + z (FP32)
 static double diag_bytes(int P) { return (P == 0 || P == 3) ? 576.0 : 288.0; }
 
-template <int P, int SELF, int POST>
-__global__ void __launch_bounds__(kThreads, (P == 3 ? 4 : 1)) k_hop(Geo g, HopDev a) {
+// MINB: resident blocks per SM the register allocation must allow (launch bound);
+// the double-float kernel is compiled for several and the fastest is picked per lattice
+template <int P, int SELF, int POST, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_hop(Geo g, HopDev a) {
     using R = typename Prec<P>::real;
     using CH = typename Prec<P>::chunk;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -91,19 +94,65 @@ __global__ void __launch_bounds__(kThreads) k_diag(Geo g, const void* __restrict
 
 // --- host dispatch ---------------------------------------------------------------
 template <int P, int SELF, int POST>
-static void launch_hop_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st) {
+static void launch_hop_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st, int minb) {
     dim3 grid(nblocks(g.Vh), nrhs);
-    k_hop<P, SELF, POST><<<grid, kThreads, 0, st>>>(g, d);
+    if constexpr (P == 3) {
+        if (minb == 2) k_hop<P, SELF, POST, 2><<<grid, kThreads, 0, st>>>(g, d);
+        else if (minb == 3) k_hop<P, SELF, POST, 3><<<grid, kThreads, 0, st>>>(g, d);
+        else k_hop<P, SELF, POST, 4><<<grid, kThreads, 0, st>>>(g, d);
+    } else {
+        k_hop<P, SELF, POST, 1><<<grid, kThreads, 0, st>>>(g, d);
+    }
 }
 
 template <int P>
-static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int nrhs, cudaStream_t st) {
-    if (self == 0 && post == 0) launch_hop_t<P, 0, 0>(g, d, nrhs, st);
-    else if (self == 0 && post == 1) launch_hop_t<P, 0, 1>(g, d, nrhs, st);
-    else if (self == 1 && post == 0) launch_hop_t<P, 1, 0>(g, d, nrhs, st);
-    else if (self == 1 && post == 1) launch_hop_t<P, 1, 1>(g, d, nrhs, st);
-    else if (self == 2 && post == 0) launch_hop_t<P, 2, 0>(g, d, nrhs, st);
-    else launch_hop_t<P, 2, 1>(g, d, nrhs, st);
+static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int nrhs, cudaStream_t st,
+                         int minb = 1) {
+    if (self == 0 && post == 0) launch_hop_t<P, 0, 0>(g, d, nrhs, st, minb);
+    else if (self == 0 && post == 1) launch_hop_t<P, 0, 1>(g, d, nrhs, st, minb);
+    else if (self == 1 && post == 0) launch_hop_t<P, 1, 0>(g, d, nrhs, st, minb);
+    else if (self == 1 && post == 1) launch_hop_t<P, 1, 1>(g, d, nrhs, st, minb);
+    else if (self == 2 && post == 0) launch_hop_t<P, 2, 0>(g, d, nrhs, st, minb);
+    else launch_hop_t<P, 2, 1>(g, d, nrhs, st, minb);
+}
+
+// Double-float hop: the launch bound (2, 3 or 4 resident blocks per SM, i.e. up
+// to 255, 168 or 128 registers per thread) is chosen per (mode, nrhs, lattice) by
+// timing the three on the caller's data on first use (the kernel reads its
+// inputs and writes a distinct output, so repeating it is harmless); the choice
+// is cached in the context like the multi-right-hand-side shapes.
+static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cudaStream_t st) {
+    const Geo& g = ctx->g;
+    const auto key = std::make_tuple((int)QXD_DF64, a.self_mode, a.post_mode, a.nrhs, (long long)g.Vh);
+    auto it = ctx->tune_hop.find(key);
+    int minb = 4;
+    if (it != ctx->tune_hop.end()) {
+        minb = it->second.first;
+    } else if (!t_no_autotune) {
+        cudaEvent_t e0, e1;
+        QXD_CUDA(ctx, cudaEventCreate(&e0));
+        QXD_CUDA(ctx, cudaEventCreate(&e1));
+        float best = 1e30f;
+        for (int mb : {2, 3, 4}) {
+            launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
+            QXD_CUDA(ctx, cudaEventRecord(e0, st));
+            for (int rep = 0; rep < 3; ++rep) launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
+            QXD_CUDA(ctx, cudaEventRecord(e1, st));
+            QXD_CUDA(ctx, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            QXD_CUDA(ctx, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                minb = mb;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->tune_hop.emplace(key, std::make_pair(minb, kThreads));
+    }
+    launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, minb);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
 }
 
 int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st) {
@@ -157,7 +206,7 @@ int launch_hop(qxd_ctx* ctx, int fl, int prec, const HopArgs& a, cudaStream_t st
         return launch_hop_mr(ctx, prec, d, a, st, &nr);
     }
     if (prec == QXD_FP64) launch_hop_p<0>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
-    else if (prec == QXD_DF64) launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
+    else if (prec == QXD_DF64) return launch_hop_df64(ctx, d, a, st);
     else if (prec == QXD_FP32) launch_hop_p<1>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
     else launch_hop_p<2>(g, d, a.self_mode, a.post_mode, a.nrhs, st);
     QXD_CUDA(ctx, cudaGetLastError());

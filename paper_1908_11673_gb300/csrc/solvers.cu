@@ -251,13 +251,16 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             if (!rz) QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, r, Z[k], ztmp, st));
             const void* rk = rz ? Z[k] : r;  // current residual
             QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Z[k], W[k], to, st));
-            // <W_j, w_k> for j < k and <r, w_k>
+            // <W_j, w_k> for j < k and <r, w_k>; without a preconditioner also |w_k|^2,
+            // from which |w_k'|^2 of the orthogonalised w_k' follows (the W_j are
+            // orthogonal), so that orthogonalisation and residual update run as one pass
             for (int j = 0; j < k; ++j) Wc[j] = W[j];
             int nd = k;
             if (!split) Wc[nd++] = rk;
+            if (rz) Wc[nd++] = W[k];
             if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), W[k], 0, st));
             if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, r, W[k], 2 * k, st));
-            QXD_TRY(blas_fetch(ctx, 2 * (k + 1), st));
+            QXD_TRY(blas_fetch(ctx, 2 * nd + (split ? 2 : 0), st));
             for (int j = 0; j < k; ++j) {
                 Rre[j * nkv + k] = ctx->red_host[2 * j] / ww[j];
                 Rim[j * nkv + k] = ctx->red_host[2 * j + 1] / ww[j];
@@ -266,12 +269,27 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             }
             // <w_k, r> = conj(<r, w_k>); r is orthogonal to the earlier w_j
             const double wr_re = ctx->red_host[2 * k], wr_im = -ctx->red_host[2 * k + 1];
-            {
-                std::vector<const void*> Wp(W.begin(), W.begin() + k);
-                QXD_TRY(blas_multi_axpy_norm(ctx, Pb, n, k, cre.data(), cim.data(), Wp.data(), W[k], 0, st));
+            std::vector<const void*> Wp(W.begin(), W.begin() + k);
+            bool fused = false;
+            if (rz) {
+                // |w_k'|^2 = |w_k|^2 - sum_j |<W_j, w_k>|^2 / |W_j|^2, used unless it cancels
+                // to less than a hundredth of |w_k|^2 (then it is summed directly below)
+                const double w2 = ctx->red_host[2 * (k + 1)];
+                double w2o = w2;
+                for (int j = 0; j < k; ++j)
+                    w2o -= (ctx->red_host[2 * j] * ctx->red_host[2 * j] + ctx->red_host[2 * j + 1] * ctx->red_host[2 * j + 1]) /
+                           ww[j];
+                if (std::isfinite(w2o) && w2o > 0.01 * w2) {
+                    fused = true;
+                    ww[k] = w2o;
+                    ctx->red_host[1] = 0.0;  // non-finite count: the dot pass found none
+                }
             }
-            QXD_TRY(blas_fetch(ctx, 2, st));
-            ww[k] = ctx->red_host[0];
+            if (!fused) {
+                QXD_TRY(blas_multi_axpy_norm(ctx, Pb, n, k, cre.data(), cim.data(), Wp.data(), W[k], 0, st));
+                QXD_TRY(blas_fetch(ctx, 2, st));
+                ww[k] = ctx->red_host[0];
+            }
             if (verbose())
                 std::fprintf(stderr, "[qxd gcr] it %d k %d |w|^2 %.6e <w,r> (%.6e, %.6e) rr %.6e nonfinite %g\n", *iters,
                              k, ww[k], wr_re, wr_im, rr, ctx->red_host[1]);
@@ -279,7 +297,10 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
             if (!(ww[k] > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
             are[k] = wr_re / ww[k];
             aim[k] = wr_im / ww[k];
-            if (rz) QXD_TRY(blas_axpy3(ctx, Pb, n, -are[k], -aim[k], W[k], Z[k], k + 1 < nkv ? Z[k + 1] : r, st));
+            if (fused)
+                QXD_TRY(blas_gcr_update(ctx, Pb, n, k, cre.data(), cim.data(), Wp.data(), W[k], -are[k], -aim[k], Z[k],
+                                        k + 1 < nkv ? Z[k + 1] : r, st));
+            else if (rz) QXD_TRY(blas_axpy3(ctx, Pb, n, -are[k], -aim[k], W[k], Z[k], k + 1 < nkv ? Z[k + 1] : r, st));
             else QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[k], -aim[k], W[k], 1.0, 0.0, r, st));
             rr -= (wr_re * wr_re + wr_im * wr_im) / ww[k];
             *iters += 1;
