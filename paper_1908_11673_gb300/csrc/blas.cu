@@ -736,7 +736,12 @@ static void gcr_update_k(qxd_ctx* ctx, int k, size_t nch, const MultiPtr& X, con
 
 int blas_gcr_update(qxd_ctx* ctx, int p, size_t n, int k, const double* cre, const double* cim,
                     const void* const* X, void* w, double ar, double ai, const void* x, void* z, cudaStream_t st) {
-    if (k > kMultiMax) return qxd_fail(ctx, QXD_EARG, "blas_gcr_update: at most 8 basis vectors");
+    if (k > kMultiMax) {
+        // all but the last eight basis vectors in a separate pass
+        const int k0 = k - kMultiMax;
+        QXD_TRY(blas_multi_axpy(ctx, p, p, n, k0, cre, cim, X, w, st));
+        return blas_gcr_update(ctx, p, n, kMultiMax, cre + k0, cim + k0, X + k0, w, ar, ai, x, z, st);
+    }
     MultiPtr mp;
     MultiCoef mc;
     for (int j = 0; j < kMultiMax; ++j) {
