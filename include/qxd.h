@@ -293,14 +293,17 @@ int qxd_apply_Dhat_eo_noalloc(qxd_ctx* ctx, int fl, int prec, int dagger, const 
                               void* stream);
 
 /* Learned preconditioner weights for flavour fl (used by FGCR with
- * QXD_PRECOND_LEARNED).  The network M has nlayers gauge-covariant layers
+ * QXD_PRECOND_LEARNED), and the precision of the network's channel mixing inside
+ * the solver: QXD_FP32 (CUDA cores, FP32) or QXD_BF16 (tensor cores: transports and
+ * weights rounded to bfloat16, FP32 accumulation; layers with at most 8 input and 8
+ * output channels, wider ones run in FP32).  The network M has nlayers gauge-covariant layers
  *   psi'_c(x) = sum_{c'} sum_{d=0..8} W[l][c][c'][d] T_d psi_{c'}(x),
  * T_0 = 1, T_{1+mu} psi(x) = V_mu(x) psi(x+mu), T_{5+mu} psi(x) = V_mu(x-mu)^+ psi(x-mu),
  * with V = U z^qhat and the boundary conditions of D; channel counts
  * 1 -> nch -> ... -> nch -> 1.  W: float32 complex, per layer
  * [cout][cin][9][4][4] spin matrices (interleaved re, im), layers one after the
  * other.  The network is not part of the paper. */
-int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch);
+int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, int prec);
 
 /* ---- SAP preconditioner (Sec. 4.1 and 4.4: SAP+GCR) ----
  * Blocks of 4^4 sites coloured like a checkerboard; one application M eta runs
@@ -362,9 +365,11 @@ int qxd_dfl_apply(qxd_ctx* ctx, int fl, const void* in, void* out, qxd_info* inf
  * every array may be host or device memory. */
 
 /* out_e = (M in_e)_e: the network applied to in_e embedded in the full lattice
- * (zero on odd sites), restricted to the even sites.  Synchronises `stream`. */
-int qxd_ptc_apply(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* in_e, void* out_e,
-                  void* stream);
+ * (zero on odd sites), restricted to the even sites; channel mixing in prec
+ * (QXD_FP32 or QXD_BF16, as in qxd_set_precond_weights).  Synchronises `stream`;
+ * QXD_ECUDA if a tensor-core completion wait timed out. */
+int qxd_ptc_apply(qxd_ctx* ctx, int fl, int prec, const float* W, int nlayers, int nch, const void* in_e,
+                  void* out_e, void* stream);
 
 /* Loss L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2 over npairs pairs (r, e:
  * [npairs][V/2][4][3] complex64) into *loss, and, if grad != NULL, its gradient

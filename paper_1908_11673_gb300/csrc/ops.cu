@@ -107,14 +107,14 @@ int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z,
         const QxdFlavour& F = ctx->fl[fl];
         if (!F.W) return qxd_fail(ctx, QXD_ESTATE, "learned preconditioner weights not set");
         const float2* W = reinterpret_cast<const float2*>(F.W);
-        if (P == QXD_FP32) return ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r, z, st);
+        if (P == QXD_FP32) return ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r, z, st, F.wprec);
         // other precisions go through FP32 copies
         void *r32, *z32;
         const size_t n = 12ull * ctx->g.Vh;
         QXD_TRY(qxd_ws(ctx, WS_PTC + 50, half_bytes(ctx, QXD_FP32), &r32));
         QXD_TRY(qxd_ws(ctx, WS_PTC + 51, half_bytes(ctx, QXD_FP32), &z32));
         QXD_TRY(blas_axpby(ctx, P, QXD_FP32, n, 1.0, 0.0, r, 0.0, 0.0, r32, st));
-        QXD_TRY(ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r32, z32, st));
+        QXD_TRY(ptc_apply_internal(ctx, fl, W, F.nlayers, F.nch, r32, z32, st, F.wprec));
         return blas_axpby(ctx, QXD_FP32, P, n, 1.0, 0.0, z32, 0.0, 0.0, z, st);
     }
     return qxd_fail(ctx, QXD_EARG, "unknown preconditioner kind");

@@ -30,9 +30,10 @@ int op_odd_reconstruct(qxd_ctx* ctx, int fl, int P, const void* r_o, const void*
 // z = M r (identity or the learned preconditioner)
 int apply_precond(qxd_ctx* ctx, int fl, int P, int kind, const void* r, void* z, cudaStream_t st);
 
-// learned preconditioner (ptc.cu): z_e = (M r_e)_e on FP32 internal even fields
+// learned preconditioner (ptc.cu): z_e = (M r_e)_e on FP32 internal even fields, the
+// channel mixing in FP32 (prec QXD_FP32) or on the tensor cores in bfloat16 (QXD_BF16)
 int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const void* r_e, void* z_e,
-                       cudaStream_t st);
+                       cudaStream_t st, int prec = QXD_FP32);
 
 // SAP preconditioner (sap.cu): z_e = (M_SAP (r_e, 0))_e on FP32 internal even fields
 int sap_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st);

@@ -326,6 +326,314 @@ __global__ void k_ptc_wgrad_final(const float2* __restrict__ partials, int nblk,
     }
 }
 
+// ---- forward layer on the tensor cores (tcgen05) ------------------------------------
+// The channel mixing of a layer is, per colour row i, the dense product
+//   out_i[site][(c,s)] = sum_d sum_{(c',s')} W[c][c'][d][s][s'] (T_d a_{c'})_i[site][s'],
+// written over the reals ([Re, Im] of the transports times the 2 x 2 real form of
+// each complex weight): M = 128 sites of a tile, N = 2*4*COUTP, K = 2*4*CINP per
+// direction d.  A CTA of 256 threads forms the transports of one direction for its
+// tile (thread = site and half of the input channels), rounds them to bfloat16 into
+// shared memory in the canonical K-major layout (8-row x 16-byte core matrices),
+// and one thread issues the tcgen05.mma instructions for the three colour rows,
+// accumulating in FP32 in tensor memory (three N-column accumulators), while the
+// other threads form the next direction's transports into a second buffer (an
+// mbarrier signalled by tcgen05.commit says when a buffer is free again).  After
+// the nine directions the accumulators are read back with tcgen05.ld and stored as
+// the output channels.  The weights, as bfloat16 real matrices, stay in shared memory
+// for all tiles of the persistent CTA.  Every wait on an mbarrier is bounded: on a
+// time-out the CTA flags the error, writes NaN to its tile, releases its tensor
+// memory and returns.
+constexpr int kTcThreads = 256;
+constexpr int kTcRows = 128;      // sites per tile (MMA M)
+constexpr int kTcTmemCols = 256;  // three accumulators of up to 64 columns
+constexpr unsigned kTcSpin = 1u << 20;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) of a K-major bfloat16 tile with K columns in the
+// canonical no-swizzle layout: core matrices of 8 rows x 8 elements (16 bytes per
+// row, 128 bytes each), adjacent along K 128 bytes apart, along rows 16 K bytes apart
+__host__ __device__ constexpr uint32_t tc_off(int row, int k, int K) {
+    return (uint32_t)((row >> 3) * (K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (row-group) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, int K) {
+    const uint64_t lbo = 128, sbo = (uint64_t)K * 16;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator, bfloat16 A and B, both
+// K-major, N and M
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// bounded wait for the completion of the phase with the given parity; false on time-out
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+    for (unsigned it = 0; it < kTcSpin; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ uint32_t bf2(float lo, float hi) { return pack_bf16x2(lo, hi); }
+
+template <int CINP, int COUTP>
+struct TcShape {
+    static constexpr int K = 8 * CINP;                  // K per direction
+    static constexpr int N = 8 * COUTP;                 // output columns per colour
+    static constexpr int A_BYTES = kTcRows * K * 2;     // one colour's A tile
+    static constexpr int B_BYTES = N * K * 2;           // one direction's B tile
+    static constexpr size_t SMEM = 2ull * 3 * A_BYTES + 9ull * B_BYTES + 64;
+};
+
+// transports of direction d for this thread's site and input channels c0, c0 + 1
+// (zero beyond cin or past the lattice), rounded to bfloat16 into A[colour]
+template <int CINP>
+__device__ __forceinline__ void tc_produce_pair(const Geo& g, int d, int p, int h, bool live, const PtcLink& lk,
+                                                const float4* __restrict__ a, int cin, int c0, int row,
+                                                unsigned char* Abuf) {
+    constexpr int K = 8 * CINP;
+    const size_t chs = (size_t)12 * g.Vh;
+    cplx<float> t[2][12];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int c = c0 + q;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) t[q][k] = {0.f, 0.f};
+        if (!live || c >= cin) continue;
+        const float4* ach = a + c * chs;
+        if (d == 0) {
+            load_spinor<1>(ach + (size_t)p * 6 * g.Vh, g.Vh, h, t[q]);
+            continue;
+        }
+        cplx<float> s[12];
+        load_spinor<1>(ach + (size_t)(1 - p) * 6 * g.Vh, g.Vh, lk.src, s);
+        const bool fwd = d <= 4;
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (fwd) cmac(acc, lk.m.a[i][j], s[3 * sp + j]);
+                    else cmac_conj(acc, lk.m.a[j][i], s[3 * sp + j]);
+                }
+                t[q][3 * sp + i] = fwd ? lk.z * acc : cmul_conj(lk.z, acc);
+            }
+    }
+    // K index (ri, c', s') -> ri * 4 CINP + 4 c' + s': channels c0, c0 + 1 fill one
+    // 16-byte chunk of real parts and one of imaginary parts per colour row
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        unsigned char* A = Abuf + i * (kTcRows * K * 2);
+        uint4 re, im;
+        re.x = bf2(t[0][i].re, t[0][3 + i].re);
+        re.y = bf2(t[0][6 + i].re, t[0][9 + i].re);
+        re.z = bf2(t[1][i].re, t[1][3 + i].re);
+        re.w = bf2(t[1][6 + i].re, t[1][9 + i].re);
+        im.x = bf2(t[0][i].im, t[0][3 + i].im);
+        im.y = bf2(t[0][6 + i].im, t[0][9 + i].im);
+        im.z = bf2(t[1][i].im, t[1][3 + i].im);
+        im.w = bf2(t[1][6 + i].im, t[1][9 + i].im);
+        *reinterpret_cast<uint4*>(A + tc_off(row, 4 * c0, K)) = re;
+        *reinterpret_cast<uint4*>(A + tc_off(row, 4 * CINP + 4 * c0, K)) = im;
+    }
+}
+
+template <int CINP, int COUTP>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_ptc_fwd_tc(Geo g, PtcLinks L, const float4* __restrict__ a, int cin, int cout, const float2* __restrict__ W,
+                 float4* __restrict__ out, int* __restrict__ err) {
+    using S = TcShape<CINP, COUTP>;
+    constexpr int K = S::K, N = S::N;
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* Abuf[2] = {tc_smem, tc_smem + 3 * S::A_BYTES};
+    unsigned char* Bsm = tc_smem + 6 * S::A_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Bsm + 9 * S::B_BYTES);
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(mbar + 2);
+    int* bad = reinterpret_cast<int*>(tmem_holder + 1);
+    const int tid = threadIdx.x;
+    const int c_out0 = blockIdx.z * COUTP;
+    const int ng = min(COUTP, cout - c_out0);
+    // weights: B_d[n][k], n = (ro, c, s), k = (ri, c', s'), the real form of W[c][c'][d][s][s']
+    for (int e = tid; e < 9 * N * K; e += kTcThreads) {
+        const int k = e % K, n = (e / K) % N, d = e / (K * N);
+        const int ri = k / (4 * CINP), cp = (k / 4) % CINP, sp = k % 4;
+        const int ro = n / (4 * COUTP), c = (n / 4) % COUTP, so = n % 4;
+        float v = 0.f;
+        if (c < ng && cp < cin) {
+            const float2 w = W[((size_t)((c_out0 + c) * cin + cp) * 9 + d) * 16 + so * 4 + sp];
+            v = (ro == ri) ? w.x : (ro == 0 ? -w.y : w.y);
+        }
+        *reinterpret_cast<__nv_bfloat16*>(Bsm + d * S::B_BYTES + tc_off(n, k, K)) = __float2bfloat16_rn(v);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *bad = 0;
+    }
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_holder;
+    constexpr uint32_t idesc = tc_idesc(kTcRows, N);
+    uint32_t phase[2] = {0u, 0u};
+    const int row = tid % kTcRows;
+    const int half = tid / kTcRows;  // input channels 4 half .. 4 half + 3
+    const int tiles = (g.Vh + kTcRows - 1) / kTcRows;
+    bool failed = false;
+    for (int tile = blockIdx.x; tile < 2 * tiles && !failed; tile += gridDim.x) {
+        const int p = tile / tiles;
+        const int h = (tile % tiles) * kTcRows + row;
+        const bool live = h < g.Vh;
+        int x[4] = {0, 0, 0, 0};
+        if (live) site_coords(g, p, h, x);
+        for (int d = 0; d < 9; ++d) {
+            const int b = d & 1;
+            if (d >= 2) {
+                // the MMAs of direction d - 2 read this buffer
+                const bool ok = tc_wait(smem_u32(&mbar[b]), phase[b]);
+                phase[b] ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
+            }
+            PtcLink lk;
+            if (live && d > 0) link_for(g, L, d, p, h, x, lk);
+            if (CINP == 2) {
+                if (half == 0) tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 0, row, Abuf[b]);
+            } else {
+                tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 4 * half, row, Abuf[b]);
+                tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 4 * half + 2, row, Abuf[b]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const uint32_t a_base = smem_u32(Abuf[b] + i * S::A_BYTES);
+                    const uint32_t b_base = smem_u32(Bsm + d * S::B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < K / 16; ++kk)
+                        tc_mma(tmem + (uint32_t)(i * 64), tc_desc(a_base + kk * 256, K), tc_desc(b_base + kk * 256, K),
+                               idesc, (d > 0 || kk > 0) ? 1 : 0);
+                }
+                tc_commit(smem_u32(&mbar[b]));
+            }
+        }
+        if (failed) break;
+        // all MMAs of the tile: the commits of directions 7 and 8
+        bool ok = tc_wait(smem_u32(&mbar[1]), phase[1]);
+        phase[1] ^= 1u;
+        ok = tc_wait(smem_u32(&mbar[0]), phase[0]) && ok;
+        phase[0] ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // epilogue: warp w reads lanes 32 (w % 4) ..; warps 0-3 colours 0 and 1, warps 4-7 colour 2
+        const int warp = tid >> 5, lane = tid & 31;
+        const int q = warp & 3;
+        const int site = 32 * q + lane;
+        const int hs = (tile % tiles) * kTcRows + site;
+        const size_t chs = (size_t)12 * g.Vh;
+        for (int i = (warp < 4 ? 0 : 2); i < (warp < 4 ? 2 : 3); ++i) {
+            float v[N];
+#pragma unroll
+            for (int c16 = 0; c16 < N / 16; ++c16)
+                tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(i * 64 + 16 * c16), v + 16 * c16);
+            if (hs < g.Vh) {
+#pragma unroll
+                for (int c = 0; c < COUTP; ++c) {
+                    if (c >= ng) break;
+                    float2* o = reinterpret_cast<float2*>(out + (c_out0 + c) * chs + (size_t)p * 6 * g.Vh);
+#pragma unroll
+                    for (int sp = 0; sp < 4; ++sp) {
+                        const int qq = 3 * sp + i;
+                        o[2 * ((size_t)(qq >> 1) * g.Vh + hs) + (qq & 1)] =
+                            make_float2(v[4 * c + sp], v[4 * COUTP + 4 * c + sp]);
+                    }
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
+    if (failed) {
+        // a wait timed out: flag it, give the tensor cores a bounded time to finish, and
+        // leave NaN in this CTA's first tile so that a solver using the output stops
+        if (tid == 0) {
+            atomicExch(err, 1);
+            tc_wait(smem_u32(&mbar[0]), phase[0]);
+            tc_wait(smem_u32(&mbar[1]), phase[1]);
+        }
+        const int tiles_ = (g.Vh + kTcRows - 1) / kTcRows;
+        const int p = blockIdx.x / tiles_;
+        const int hs = (blockIdx.x % tiles_) * kTcRows + row;
+        if (half == 0 && p < 2 && hs < g.Vh) {
+            const size_t chs = (size_t)12 * g.Vh;
+            for (int c = 0; c < ng; ++c)
+                for (int k = 0; k < 6; ++k)
+                    out[(c_out0 + c) * chs + (size_t)p * 6 * g.Vh + (size_t)k * g.Vh + hs] =
+                        make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+    }
+    if (tid < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    (void)bad;
+}
+
 // Adam on the real view of W: gradient = scale * 2 (Re G, Im G)
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ G, float* __restrict__ m, float* __restrict__ v,
                        size_t n, float scale, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -378,6 +686,38 @@ static int launch_layer(qxd_ctx* ctx, int fl, const float4* a, int cin, const fl
     return launch_fwd<8>(ctx, fl, a, cin, W, out, cout, st);
 }
 
+// one forward layer on the tensor cores (bfloat16 operands, FP32 accumulation): input
+// channels padded to 2 or 8, output channels in groups of 2 or 8 (grid.z); at most
+// two CTAs per SM (each holds 256 of the SM's 512 tensor-memory columns)
+template <int CINP, int COUTP>
+static int launch_fwd_tc(qxd_ctx* ctx, int fl, const float4* a, int cin, const float2* W, float4* out, int cout,
+                         cudaStream_t st) {
+    const Geo& g = ctx->g;
+    const size_t smem = std::max<size_t>(TcShape<CINP, COUTP>::SMEM, 100 * 1024);
+    QXD_CUDA(ctx, cudaFuncSetAttribute(k_ptc_fwd_tc<CINP, COUTP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+    const int groups = (cout + COUTP - 1) / COUTP;
+    const int tiles = 2 * ((g.Vh + kTcRows - 1) / kTcRows);
+    int per_sm = 0;
+    QXD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ptc_fwd_tc<CINP, COUTP>, kTcThreads, smem));
+    per_sm = std::max(1, std::min(per_sm, 2));
+    const int nx = std::max(1, std::min(tiles, per_sm * ctx->nsm / groups));
+    k_ptc_fwd_tc<CINP, COUTP><<<dim3(nx, 1, groups), kTcThreads, smem, st>>>(g, links_of(ctx, fl), a, cin, cout, W,
+                                                                             out, ctx->dev_flag);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+
+static int launch_layer_tc(qxd_ctx* ctx, int fl, const float4* a, int cin, const float2* W, float4* out, int cout,
+                           cudaStream_t st) {
+    if (cin > 8 || cout > 8) return launch_layer(ctx, fl, a, cin, W, out, cout, st);
+    ProfScope prof(ctx, "ptc_layer_tc", layer_bytes(ctx, cin, cout), st);
+    if (cin <= 2 && cout <= 2) return launch_fwd_tc<2, 2>(ctx, fl, a, cin, W, out, cout, st);
+    if (cin <= 2) return launch_fwd_tc<2, 8>(ctx, fl, a, cin, W, out, cout, st);
+    if (cout <= 2) return launch_fwd_tc<8, 2>(ctx, fl, a, cin, W, out, cout, st);
+    return launch_fwd_tc<8, 8>(ctx, fl, a, cin, W, out, cout, st);
+}
+
 // weight gradient of one layer into G (accumulated): grid (blocks, 1, chunks)
 static int wgrad_blocks(const qxd_ctx* ctx) {
     const int tiles = 2 * ((ctx->g.Vh + kPtcSites - 1) / kPtcSites);
@@ -403,14 +743,16 @@ static int launch_wgrad(qxd_ctx* ctx, int fl, const float4* delta, const float4*
     return QXD_OK;
 }
 
-// Forward pass: acts[0] = embedded input (1 channel); acts[l+1] = layer l (acts[l])
+// Forward pass: acts[0] = embedded input (1 channel); acts[l+1] = layer l (acts[l]).
+// prec QXD_FP32: CUDA-core FP32 layers; QXD_BF16: the channel mixing on the tensor cores
 static int ptc_forward(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, float4* const* acts,
-                       cudaStream_t st) {
+                       cudaStream_t st, int prec = QXD_FP32) {
     const float2* w = W;
     for (int l = 0; l < nlayers; ++l) {
         int ci, co;
         layer_shape(l, nlayers, nch, &ci, &co);
-        QXD_TRY(launch_layer(ctx, fl, acts[l], ci, w, acts[l + 1], co, st));
+        if (prec == QXD_BF16) QXD_TRY(launch_layer_tc(ctx, fl, acts[l], ci, w, acts[l + 1], co, st));
+        else QXD_TRY(launch_layer(ctx, fl, acts[l], ci, w, acts[l + 1], co, st));
         w += layer_weights(ci, co);
     }
     return QXD_OK;
@@ -434,15 +776,16 @@ static int ptc_buffers(qxd_ctx* ctx, int nlayers, int nch, int slot0, std::vecto
     return QXD_OK;
 }
 
-// z_e = (M r_e)_e for FP32 internal even fields
+// z_e = (M r_e)_e for FP32 internal even fields (prec: QXD_FP32 or QXD_BF16 mixing)
 int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const void* r_e, void* z_e,
-                       cudaStream_t st) {
+                       cudaStream_t st, int prec) {
     std::vector<float4*> acts;
     QXD_TRY(ptc_buffers(ctx, nlayers, nch, WS_PTC, acts));
     const size_t hb = half_bytes(ctx, QXD_FP32);
     QXD_CUDA(ctx, cudaMemcpyAsync(acts[0], r_e, hb, cudaMemcpyDeviceToDevice, st));
     QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(acts[0]) + hb, 0, hb, st));
-    QXD_TRY(ptc_forward(ctx, fl, W, nlayers, nch, acts.data(), st));
+    if (prec == QXD_BF16) QXD_CUDA(ctx, cudaMemsetAsync(ctx->dev_flag, 0, sizeof(int), st));
+    QXD_TRY(ptc_forward(ctx, fl, W, nlayers, nch, acts.data(), st, prec));
     QXD_CUDA(ctx, cudaMemcpyAsync(z_e, acts[nlayers], hb, cudaMemcpyDeviceToDevice, st));
     return QXD_OK;
 }
@@ -557,9 +900,11 @@ static int ptc_check(qxd_ctx* ctx, int fl) {
 
 extern "C" {
 
-int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch) {
+int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, int prec) {
     QXD_TRY(ptc_check(ctx, fl));
     QXD_TRY(check_shape(ctx, nlayers, nch));
+    if (prec != QXD_FP32 && prec != QXD_BF16)
+        return qxd_fail(ctx, QXD_EARG, "set_precond_weights: precision must be QXD_FP32 or QXD_BF16");
     if (!W) return qxd_fail(ctx, QXD_EARG, "set_precond_weights: NULL weights");
     QxdFlavour& F = ctx->fl[fl];
     const size_t nw = ptc_weight_count(nlayers, nch);
@@ -572,14 +917,17 @@ int qxd_set_precond_weights(qxd_ctx* ctx, int fl, const float* W, int nlayers, i
     QXD_CUDA(ctx, cudaMemcpy(F.W, W, nw * sizeof(float2), cudaMemcpyDefault));
     F.nlayers = nlayers;
     F.nch = nch;
+    F.wprec = prec;
     return QXD_OK;
 }
 
-int qxd_ptc_apply(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* in_e, void* out_e,
-                  void* stream) {
+int qxd_ptc_apply(qxd_ctx* ctx, int fl, int prec, const float* W, int nlayers, int nch, const void* in_e,
+                  void* out_e, void* stream) {
     QXD_TRY(ptc_check(ctx, fl));
     QXD_TRY(check_shape(ctx, nlayers, nch));
     if (!W || !in_e || !out_e) return qxd_fail(ctx, QXD_EARG, "ptc_apply: NULL argument");
+    if (prec != QXD_FP32 && prec != QXD_BF16)
+        return qxd_fail(ctx, QXD_EARG, "ptc_apply: precision must be QXD_FP32 or QXD_BF16");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t cb = (size_t)ctx->g.Vh * 12 * 8;
     const size_t hb = half_bytes(ctx, QXD_FP32);
@@ -592,10 +940,15 @@ int qxd_ptc_apply(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, co
     QXD_TRY(qxd_ws(ctx, WS_PTC + 34, cb, &co));
     QXD_CUDA(ctx, cudaMemcpyAsync(ci, in_e, cb, cudaMemcpyDefault, st));
     QXD_TRY(launch_pack(ctx, 1, ci, 0, 0, QXD_FP32, ri, 1, st));
-    QXD_TRY(ptc_apply_internal(ctx, fl, Wd, nlayers, nch, ri, zi, st));
+    QXD_TRY(ptc_apply_internal(ctx, fl, Wd, nlayers, nch, ri, zi, st, prec));
     QXD_TRY(launch_unpack(ctx, QXD_FP32, zi, 0, 1, co, 0, 1, st));
     QXD_CUDA(ctx, cudaMemcpyAsync(out_e, co, cb, cudaMemcpyDefault, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    if (prec == QXD_BF16) {
+        int flag = 0;
+        QXD_CUDA(ctx, cudaMemcpy(&flag, ctx->dev_flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) return qxd_fail(ctx, QXD_ECUDA, "ptc_apply: a tensor-core completion wait timed out");
+    }
     return QXD_OK;
 }
 

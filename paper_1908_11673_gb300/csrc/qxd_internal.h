@@ -25,6 +25,7 @@ struct QxdFlavour {
     // learned preconditioner
     void* W = nullptr;         // device weights (complex float [layers][cout][cin][9][4][4])
     int nlayers = 0, nch = 0;
+    int wprec = QXD_BF16;      // precision of the network's channel mixing inside FGCR
     // deflation subspace (qxd_dfl_setup)
     float4* dfl_basis = nullptr;  // [Ns] full FP32 fields, block-orthonormal
     float2* dfl_A = nullptr;      // little operator [Nb][9][Ns][Ns]

@@ -106,10 +106,10 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_apply_Dhat_eo_noalloc": (i, [vp, i, i, i, vp, vp, vp]),
         "qxd_solve": (i, [vp, i, ctypes.POINTER(Solver), vp, vp, i, ctypes.POINTER(Info), vp]),
         "qxd_solve_multishift": (i, [vp, i, i, vp, ctypes.POINTER(Solver), vp, vp, ctypes.POINTER(Info), vp]),
-        "qxd_set_precond_weights": (i, [vp, i, vp, i, i]),
+        "qxd_set_precond_weights": (i, [vp, i, vp, i, i, i]),
         "qxd_set_sap": (i, [vp, i, i]),
         "qxd_sap_apply": (i, [vp, i, vp, vp, vp]),
-        "qxd_ptc_apply": (i, [vp, i, vp, i, i, vp, vp, vp]),
+        "qxd_ptc_apply": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
         "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(d), vp, vp]),
         "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, ctypes.POINTER(i), vp, vp]),
         "qxd_ptc_record_pairs": (i, [vp, i, vp, i, i, vp, vp, vp]),
@@ -366,9 +366,10 @@ class Context:
         self._check(self.lib.qxd_sap_apply(self._h, int(fl), _ptr(inp), _ptr(out), _stream(stream)))
 
     # ---- learned preconditioner ------------------------------------------------
-    def ptc_apply(self, fl, W, nlayers, nch, inp, out, stream=None):
-        self._check(self.lib.qxd_ptc_apply(self._h, int(fl), _ptr(W), int(nlayers), int(nch), _ptr(inp), _ptr(out),
-                                           _stream(stream)))
+    def ptc_apply(self, fl, W, nlayers, nch, inp, out, stream=None, prec=FP32):
+        """out_e = (M in_e)_e; prec FP32 (CUDA cores) or BF16 (tensor-core channel mixing)."""
+        self._check(self.lib.qxd_ptc_apply(self._h, int(fl), int(prec), _ptr(W), int(nlayers), int(nch), _ptr(inp),
+                                           _ptr(out), _stream(stream)))
 
     def ptc_loss_grad(self, fl, W, nlayers, nch, r, e, npairs, grad=None, stream=None):
         loss = ctypes.c_double()
@@ -407,5 +408,7 @@ class Context:
             i += 1
         return out
 
-    def set_precond_weights(self, fl, W, nlayers, nch):
-        self._check(self.lib.qxd_set_precond_weights(self._h, int(fl), _ptr(W), int(nlayers), int(nch)))
+    def set_precond_weights(self, fl, W, nlayers, nch, prec=BF16):
+        """Network weights of the learned preconditioner and the precision of its
+        channel mixing inside FGCR (BF16: tensor cores; FP32: CUDA cores)."""
+        self._check(self.lib.qxd_set_precond_weights(self._h, int(fl), _ptr(W), int(nlayers), int(nch), int(prec)))
