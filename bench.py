@@ -93,6 +93,11 @@ WORKLOADS = {
     "32^3x64-cstar3": dict(L=(64, 32, 32, 32), cstar=3, theta=(math.pi, 0.0, 0.0, 0.0), qhat=4,
                            kappa=0.137312, su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=2000,
                            src_seed=2001, stout=5, rho=0.1),
+    # the bench lattice and couplings on rougher fields (H entries N(0, 0.6^2), plaquette about 0.63
+    # after the 5 stout steps, the value the configurations aim at): the preconditioner comparison
+    "32^3x64-cstar3-rough": dict(L=(64, 32, 32, 32), cstar=3, theta=(math.pi, 0.0, 0.0, 0.0), qhat=4,
+                                 kappa=0.137312, su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=2100,
+                                 src_seed=2101, stout=5, rho=0.1, sigma_h=0.6),
     # 24^3 x 48, antiperiodic time (larger than L2, a few GB on the device: profiler captures)
     "24^3x48": dict(L=(48, 24, 24, 24), cstar=0, theta=(math.pi, 0.0, 0.0, 0.0), qhat=-2, kappa=0.136377,
                     su3csw=1.90952, u1csw=1.0, invqel=6.0, field_seed=3000, src_seed=3001, stout=5, rho=0.1),
@@ -261,7 +266,8 @@ def oracle_rate_all_cores(w, U, A, psi, seconds, single_rate):
 
 def make_inputs(w, device):
     from paper_1908_11673_gb300 import workload
-    U, A = workload.gauge_field(w["L"], w["field_seed"], stout_steps=w["stout"], rho=w["rho"], device=device)
+    U, A = workload.gauge_field(w["L"], w["field_seed"], sigma_h=w.get("sigma_h", 0.3), stout_steps=w["stout"],
+                                rho=w["rho"], device=device)
     V = int(np.prod(w["L"])) * (2 if w["cstar"] else 1)
     eta = workload.spinor(V, w["src_seed"])
     return U, A, eta
@@ -356,6 +362,71 @@ def spectral_range(ctx, qxd, torch, dev, stream, V, n_power=40, n_inverse=5):
             "inside_printed_range": bool(lam_max <= rb * rb and lam_min >= ra * ra)}
 
 
+def precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, solve_kw, V):
+    """SAP(5,5)-, SAP(3,4)- and DFL+SAP(3,4)-preconditioned FGCR (Sec. 4.4) on the
+    context's system, each timed with CUDA events (one solve after a warm-up)."""
+    nxt = {}
+    for ncy, nmr in ((5, 5), (3, 4)):
+        ctx.set_sap(ncy, nmr)
+        ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP, "nkv": 16}))
+        ctx.profile(2)
+        ms_sap, inf_sap = timed(lambda: ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP,
+                                                                                  "nkv": 16})), 1)
+        ps = {p["name"]: p for p in ctx.profile_entries()}
+        ctx.profile(0)
+        blk = ps.get("sap_sweep")
+        nxt[f"sap_fgcr_ncy{ncy}_nmr{nmr}"] = {
+            "ms": ms_sap, "iters": inf_sap[0].iters, "true_relres": inf_sap[0].true_relres,
+            "sap_sweep_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
+            "sap_sweep_launches": blk["launches"] if blk else None,
+            "sap_sweep_GBps": blk["bytes"] / (blk["ms"] * 1e-3) / 1e9 if blk else None}
+    # inexact deflation (DFL+SAP+GCR): subspace from Ns Gaussian fields drawn on the
+    # device with a seeded generator, SAP(3,4) as smoother and for the inverse iteration
+    ctx.set_sap(3, 4)
+    gen = torch.Generator(device=dev).manual_seed(4242)
+    seeds = torch.randn((12, V, 4, 3), dtype=torch.complex64, device=dev, generator=gen)
+    torch.cuda.synchronize()
+    t0d = time.perf_counter()
+    ctx.dfl_setup(0, seeds, 12, ninv=2, ctol=1e-2, cnmx=64, stream=stream)
+    torch.cuda.synchronize()
+    dfl_setup_ms = (time.perf_counter() - t0d) * 1e3
+    del seeds
+    dkw = solve_kw | {"precond": qxd.PRECOND_DFL, "nkv": 16}
+    ms_dfl, inf_dfl = timed(lambda: ctx.solve(0, eta_d, psi_d, **dkw), 1)
+    nxt["dfl_fgcr_Ns12_ninv2_sap3_4"] = {"setup_ms": dfl_setup_ms, "ms": ms_dfl, "iters": inf_dfl[0].iters,
+                                          "true_relres": inf_dfl[0].true_relres}
+    return nxt
+
+
+def rough_row(args, qxd, torch, dev, stream, timed, fp32_kw):
+    """The bench lattice and couplings on rougher synthetic fields (plaquette about
+    0.63 after smearing, the value the configurations aim at): plain FP64 CGNE,
+    the unpreconditioned mixed FGCR, SAP and DFL+SAP, and the mixed 4-RHS learned
+    batch, to 1e-10 each."""
+    from paper_1908_11673_gb300 import workload
+    w = WORKLOADS["32^3x64-cstar3-rough"]
+    U, A, eta = make_inputs(w, str(dev))
+    ctx = qxd.Context(w["L"], w["cstar"], w["theta"], device=dev.index or 0)
+    ctx.set_links(U, A, w["invqel"], stream=stream)
+    ctx.set_clover(0, w["qhat"], w["kappa"], w["su3csw"], w["u1csw"], stream=stream)
+    V = ctx.V
+    row = {"field": "H entries N(0, 0.6^2), 5 stout steps rho 0.1, seed 2100",
+           "plaquette": workload.plaquette(U, w["L"])}
+    del U, A
+    eta_d = torch.from_numpy(eta).to(dev)
+    psi_d = torch.empty_like(eta_d)
+    ctx.solve(0, eta_d, psi_d, **fp32_kw)
+    ms, inf = timed(lambda: ctx.solve(0, eta_d, psi_d, **fp32_kw), 1)
+    row["fgcr_mixed"] = {"ms": ms, "iters": inf[0].iters, "true_relres": inf[0].true_relres}
+    ms64, inf64 = timed(lambda: ctx.solve(0, eta_d, psi_d, kind=qxd.CGNE, tol=1e-10, nmx=200000, stream=stream), 1)
+    row["fp64_cgne"] = {"ms": ms64, "iters": inf64[0].iters, "true_relres": inf64[0].true_relres}
+    row.update(precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, fp32_kw, V))
+    del eta_d, psi_d
+    row["learned_batched_mixed"] = learned_row(ctx, qxd, torch, dev, stream, timed, w, V, ms64)
+    ctx.close()
+    return row
+
+
 def learned_row(ctx, qxd, torch, dev, stream, timed, w, V, fp64_cgne_ms):
     """The mixed-precision, batched, learned-preconditioned solve on the bench
     system: the network (4 layers x 8 channels) is trained on four 16 x 8^3 lattices
@@ -367,7 +438,8 @@ def learned_row(ctx, qxd, torch, dev, stream, timed, w, V, fp64_cgne_ms):
     same batch without the network, and the plain FP64 CGNE time per right-hand side."""
     from paper_1908_11673_gb300 import learned
     field = dict(L=(16, 8, 8, 8), cstar=w["cstar"], theta=w["theta"], qhat=w["qhat"], kappa=w["kappa"],
-                 su3csw=w["su3csw"], u1csw=w["u1csw"], invqel=w["invqel"], stout=w["stout"], rho=w["rho"])
+                 su3csw=w["su3csw"], u1csw=w["u1csw"], invqel=w["invqel"], stout=w["stout"], rho=w["rho"],
+                 sigma_h=w.get("sigma_h", 0.3))
     nl, nch, nrhs = 4, 8, 4
     W, summ = learned.train(field, [7000 + i for i in range(4)], 50, epochs=4, batch=10, nlayers=nl, nch=nch,
                             device=dev.index or 0)
@@ -551,35 +623,7 @@ def run_native(args, w, name):
     if not args.no_extras:
         spec = spectral_range(ctx, qxd, torch, dev, stream, V)
         nxt = {}
-        for ncy, nmr in ((5, 5), (3, 4)):
-            ctx.set_sap(ncy, nmr)
-            ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP, "nkv": 16}))
-            ctx.profile(2)
-            ms_sap, inf_sap = timed(lambda: ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP,
-                                                                                      "nkv": 16})), 1)
-            ps = {p["name"]: p for p in ctx.profile_entries()}
-            ctx.profile(0)
-            blk = ps.get("sap_sweep")
-            nxt[f"sap_fgcr_ncy{ncy}_nmr{nmr}"] = {
-                "ms": ms_sap, "iters": inf_sap[0].iters, "true_relres": inf_sap[0].true_relres,
-                "sap_sweep_ms_per_launch": blk["ms"] / blk["launches"] if blk else None,
-                "sap_sweep_launches": blk["launches"] if blk else None,
-                "sap_sweep_GBps": blk["bytes"] / (blk["ms"] * 1e-3) / 1e9 if blk else None}
-        # inexact deflation (DFL+SAP+GCR): subspace from Ns Gaussian fields drawn on the
-        # device with a seeded generator, SAP(3,4) as smoother and for the inverse iteration
-        ctx.set_sap(3, 4)
-        gen = torch.Generator(device=dev).manual_seed(4242)
-        seeds = torch.randn((12, V, 4, 3), dtype=torch.complex64, device=dev, generator=gen)
-        torch.cuda.synchronize()
-        t0d = time.perf_counter()
-        ctx.dfl_setup(0, seeds, 12, ninv=2, ctol=1e-2, cnmx=64, stream=stream)
-        torch.cuda.synchronize()
-        dfl_setup_ms = (time.perf_counter() - t0d) * 1e3
-        del seeds
-        dkw = solve_kw | {"precond": qxd.PRECOND_DFL, "nkv": 16}
-        ms_dfl, inf_dfl = timed(lambda: ctx.solve(0, eta_d, psi_d, **dkw), 1)
-        nxt["dfl_fgcr_Ns12_ninv2_sap3_4"] = {"setup_ms": dfl_setup_ms, "ms": ms_dfl, "iters": inf_dfl[0].iters,
-                                              "true_relres": inf_dfl[0].true_relres}
+        nxt.update(precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, solve_kw, V))
         A_r, nu_r, mu_r = read_rational(GOLDEN_RATIONAL)
         rat = qxd.rational(A_r, nu_r, mu_r)
         phi_e = torch.from_numpy(np.ascontiguousarray(eta[: V // 2])).to(dev)
@@ -608,6 +652,10 @@ def run_native(args, w, name):
         del eta_d, psi_d
         torch.cuda.empty_cache()
         nxt["batched_24x24x24x48"] = batched_row(qxd, torch, dev, stream, timed_local)
+        try:
+            nxt["rough_fields_32x32x32x64_cstar3"] = rough_row(args, qxd, torch, dev, stream, timed_local, solve_kw)
+        except qxd.QxdError as e:  # a solve that misses 1e-10 within nmx is reported, not fatal
+            nxt["rough_fields_32x32x32x64_cstar3"] = {"error": str(e)}
 
     peak, peak_kind = measured_peaks()
     dom = max(prof, key=lambda p: p["ms"])

@@ -43,8 +43,8 @@ def identity_weights(nlayers, nch):
 
 
 def make_context(seed, device=0, field=FIELD):
-    U, A = workload.gauge_field(field["L"], seed, stout_steps=field["stout"], rho=field["rho"],
-                                u1_stout_steps=field.get("u1_stout", 0))
+    U, A = workload.gauge_field(field["L"], seed, sigma_h=field.get("sigma_h", 0.3), stout_steps=field["stout"],
+                                rho=field["rho"], u1_stout_steps=field.get("u1_stout", 0))
     ctx = qxd.Context(field["L"], field["cstar"], field["theta"], device=device)
     ctx.set_links(U, A, field["invqel"])
     ctx.set_clover(0, field["qhat"], field["kappa"], field["su3csw"], field["u1csw"])
