@@ -18,8 +18,12 @@ preconditioner of the even-odd operator Dhat, M acts on an even-site field r
 embedded in the full lattice (zero on odd sites) and its output is restricted
 to the even sites: Dhat^-1 = (D^-1)_ee, so M is trained to approximate D^-1.
 
-Loss over pairs (r_i, e_i) with Dhat e_i = r_i:
-    L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2.
+Loss over pairs (r_i, e_i) with Dhat e_i = r_i, in one of two norms:
+    L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2                  ("error": Euclidean norm)
+    L = sum_i |r_i - Dhat (M r_i)_e|^2 / |r_i|^2            ("residual")
+The second is the error of M r_i measured in the norm |Dhat .|, since
+Dhat e_i = r_i; it weighs each mode by |Dhat|, as the residual of a right-
+preconditioned Krylov solver does, and is 1 for M = 0.
 Gradient (Wirtinger): G = dL/dW^* = sum_x delta_c(x) (T_d a_{c'}(x))^+ per
 layer, with delta = (out - e)/|e|^2 at the output and delta' = layer^+ delta
 propagated backwards (layer^+ uses W^+ and T_d^+ = T_{opposite d}).
@@ -127,27 +131,50 @@ def network(T: Transport, Ws, r_e, keep=False):
     return (out, acts) if keep else out
 
 
-def loss(T: Transport, Ws, pairs):
+def _dhat_pair(op):
+    """Dhat and Dhat^+ = gamma5 Dhat gamma5 on even-site fields."""
+    from .dirac import gamma5
+    Dinv = op.Doo_inv()
+    return (lambda v: op.Dhat(v, Dinv)), (lambda v: gamma5(op.Dhat(gamma5(v), Dinv)))
+
+
+def loss(T: Transport, Ws, pairs, norm="error"):
     tot = 0.0
+    if norm == "residual":
+        D, _ = _dhat_pair(T.op)
     for r, e in pairs:
         out = network(T, Ws, r)
-        tot += float(np.vdot(out - e, out - e).real / np.vdot(e, e).real)
+        if norm == "residual":
+            res = r - D(out)
+            tot += float(np.vdot(res, res).real / np.vdot(r, r).real)
+        else:
+            tot += float(np.vdot(out - e, out - e).real / np.vdot(e, e).real)
     return tot
 
 
-def loss_and_grad(T: Transport, Ws, pairs):
-    """L and G_l = dL/dW_l^* (complex arrays shaped like W_l)."""
+def loss_and_grad(T: Transport, Ws, pairs, norm="error"):
+    """L and G_l = dL/dW_l^* (complex arrays shaped like W_l).  The output
+    adjoint is (out - e)/|e|^2 for the Euclidean error and
+    Dhat^+ (Dhat out - r)/|r|^2 for the residual norm."""
     op = T.op
     ev = op.even_sites()
     G = [np.zeros_like(W) for W in Ws]
     tot = 0.0
+    if norm == "residual":
+        D, Ddag = _dhat_pair(op)
     for r, e in pairs:
         out, acts = network(T, Ws, r, keep=True)
-        ee = float(np.vdot(e, e).real)
-        res = out - e
-        tot += float(np.vdot(res, res).real) / ee
         delta = np.zeros((1, op.geom.V, 4, 3), dtype=np.complex128)
-        delta[0][ev] = res / ee
+        if norm == "residual":
+            rr = float(np.vdot(r, r).real)
+            res = D(out) - r
+            tot += float(np.vdot(res, res).real) / rr
+            delta[0][ev] = Ddag(res) / rr
+        else:
+            ee = float(np.vdot(e, e).real)
+            res = out - e
+            tot += float(np.vdot(res, res).real) / ee
+            delta[0][ev] = res / ee
         for l in range(len(Ws) - 1, -1, -1):
             a = acts[l]
             W = Ws[l]

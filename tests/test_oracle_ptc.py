@@ -86,15 +86,16 @@ def test_gauge_covariance_of_the_network():
     assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
 
 
-def test_gradient_matches_central_differences():
+@pytest.mark.parametrize("norm", ["error", "residual"])
+def test_gradient_matches_central_differences(norm):
     op, _, _ = make_op((2, 4, 2, 4), 1, (np.pi, 0, 0, 0), qhat=-2, seed=13)
     T = ptc.Transport(op)
     rng = np.random.default_rng(7)
     Ws = rand_weights(rng, 3, 2, scale=0.2)
     ne = op.geom.V // 2
     pairs = [(workload.spinor(ne, 20 + i), workload.spinor(ne, 40 + i)) for i in range(2)]
-    L0, G = ptc.loss_and_grad(T, Ws, pairs)
-    assert abs(L0 - ptc.loss(T, Ws, pairs)) < 1e-12 * L0
+    L0, G = ptc.loss_and_grad(T, Ws, pairs, norm=norm)
+    assert abs(L0 - ptc.loss(T, Ws, pairs, norm=norm)) < 1e-12 * L0
     h = 1e-6
     for l, c, cp, d, s, t in [(0, 1, 0, 0, 2, 3), (1, 0, 1, 3, 0, 0), (1, 1, 1, 7, 1, 2), (2, 0, 0, 5, 3, 1),
                               (2, 0, 1, 8, 2, 2)]:
@@ -103,6 +104,29 @@ def test_gradient_matches_central_differences():
             Wm = [W.copy() for W in Ws]
             Wp[l][c, cp, d, s, t] += h * part
             Wm[l][c, cp, d, s, t] -= h * part
-            fd = (ptc.loss(T, Wp, pairs) - ptc.loss(T, Wm, pairs)) / (2 * h)
+            fd = (ptc.loss(T, Wp, pairs, norm=norm) - ptc.loss(T, Wm, pairs, norm=norm)) / (2 * h)
             an = 2 * (G[l][c, cp, d, s, t].real if part == 1.0 else G[l][c, cp, d, s, t].imag)
             assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3 * L0), (l, c, cp, d, s, t, part, fd, an)
+
+
+def test_residual_norm_special_cases():
+    """The residual-norm loss of one pair: 1 for the zero map, |r - Dhat r|^2 / |r|^2
+    for the identity network (Dhat from the dense matrix of the oracle's operator),
+    and equal to the error loss weighted by Dhat, |Dhat (M r - e)|^2 / |Dhat e|^2,
+    for a pair with Dhat e = r."""
+    op, _, _ = make_op((2, 4, 2, 4), 0, (np.pi, 0, 0, 0), qhat=3, seed=17)
+    T = ptc.Transport(op)
+    ne = op.geom.V // 2
+    Dinv = op.Doo_inv()
+    Dmat = np.stack([op.Dhat(np.eye(12 * ne)[k].reshape(ne, 4, 3), Dinv).reshape(-1) for k in range(12 * ne)], axis=1)
+    e = workload.spinor(ne, 51)
+    r = (Dmat @ e.reshape(-1)).reshape(ne, 4, 3)
+    zero = [np.zeros_like(W) for W in ptc.identity_weights(3, 2)]
+    assert abs(ptc.loss(T, zero, [(r, e)], norm="residual") - 1.0) < 1e-14
+    ident = ptc.identity_weights(3, 2)
+    want = np.linalg.norm(r.reshape(-1) - Dmat @ r.reshape(-1)) ** 2 / np.linalg.norm(r) ** 2
+    assert abs(ptc.loss(T, ident, [(r, e)], norm="residual") - want) < 1e-12 * want
+    Ws = rand_weights(np.random.default_rng(9), 3, 2, scale=0.2)
+    out = ptc.network(T, Ws, r)
+    dnorm = np.linalg.norm(Dmat @ (out - e).reshape(-1)) ** 2 / np.linalg.norm(Dmat @ e.reshape(-1)) ** 2
+    assert abs(ptc.loss(T, Ws, [(r, e)], norm="residual") - dnorm) < 1e-10 * dnorm
