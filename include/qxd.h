@@ -371,21 +371,25 @@ int qxd_dfl_apply(qxd_ctx* ctx, int fl, const void* in, void* out, qxd_info* inf
 int qxd_ptc_apply(qxd_ctx* ctx, int fl, int prec, const float* W, int nlayers, int nch, const void* in_e,
                   void* out_e, void* stream);
 
-/* Loss L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2 over npairs pairs (r, e:
- * [npairs][V/2][4][3] complex64) into *loss, and, if grad != NULL, its gradient
+/* Loss over npairs pairs (r, e: [npairs][V/2][4][3] complex64) into *loss:
+ * kind 0, Euclidean error: L = sum_i |(M r_i)_e - e_i|^2 / |e_i|^2;
+ * kind 1, residual norm:   L = sum_i |r_i - Dhat (M r_i)_e|^2 / |r_i|^2 (with Dhat the
+ * FP32 operator; for pairs with Dhat e_i = r_i the error of M r_i in the norm |Dhat .|);
+ * and, if grad != NULL, its gradient
  * G = dL/dW^* (Wirtinger; the gradient with respect to the real and imaginary
  * parts of W is 2 Re G, 2 Im G), complex float32 in the layout of W. */
 int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* r, const void* e,
-                      int npairs, double* loss, float* grad, void* stream);
+                      int npairs, int kind, double* loss, float* grad, void* stream);
 
 /* nsteps steps of Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the
- * loss above, each over `batch` pairs taken in turn from the npairs given.  W is
+ * loss above (kind as there), each over `batch` pairs taken in turn from the npairs given.  W is
  * updated in place; m, v are the Adam moments (same size as W, zero at the
  * start of training) and *t the step counter, all carried between calls so
  * that training can alternate gauge fields (one context per field).
  * losses (may be NULL) receives the mean loss of each step. */
 int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayers, int nch, const void* r,
-                  const void* e, int npairs, int batch, int nsteps, double lr, int* t, double* losses, void* stream);
+                  const void* e, int npairs, int batch, int nsteps, double lr, int kind, int* t, double* losses,
+                  void* stream);
 
 /* Training pairs from the plain FP64 solver: CG on the normal equations of
  * Dhat x = b (b: complex128 [V/2][4][3]) run to |b - Dhat x| <= 1e-10 |b|; at

@@ -92,6 +92,182 @@ __global__ void __launch_bounds__(kThreads) k_diag(Geo g, const void* __restrict
     store_spinor<P>(static_cast<CH*>(out) + rhs_off, g.Vh, h, s);
 }
 
+// ---- double-float hop with two threads per site --------------------------------------
+// The pair of adjacent lanes (2k, 2k+1) shares one output site; lane `half` forms the
+// half-spinor component half of every spin projection (spins half and its partner),
+// multiplies it by the link and adds it into the output spin half (accO) and into the
+// lower spins it feeds: accP (spin 2 + half: directions 0 and 3) or accQ (spin
+// 3 - half: directions 1 and 2).  Every lane runs the same instruction stream (the
+// half only selects addresses and signs), so the pair does not diverge.  At the end
+// the lanes exchange their partial sums: lane 0 owns the upper chiral block (spins 0,
+// 1), lane 1 the lower one (spins 2, 3), each applying its 6 x 6 site-diagonal block.
+// Per lane this halves the arithmetic and the live registers of the one-thread kernel.
+using cdf = cplx<dfl>;
+
+__device__ __forceinline__ void load3_df(const float4* __restrict__ base, int Vh, int h, int sp, cdf v[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 f = QXD_LDG(base + (size_t)(3 * sp + c) * Vh + h);
+        v[c] = {dfl(f.x, f.y), dfl(f.z, f.w)};
+    }
+}
+__device__ __forceinline__ cdf mul_i(cdf a) { return {-a.im, a.re}; }
+__device__ __forceinline__ cdf scale_sign(cdf a, bool neg) { return neg ? cdf{-a.re, -a.im} : a; }
+
+// one hop direction (MU, FWD) for this lane: its half-spinor component, times the link
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_half_df(const Geo& g, const HopDev& a, const float4* __restrict__ in,
+                                            const int x[4], int h, int half, bool g5nb, cdf accO[3], cdf accP[3],
+                                            cdf accQ[3]) {
+    const int Vh = g.Vh;
+    const int n = neighbour_lex(g, x, MU, FWD ? +1 : -1) >> 1;
+    // spins of this lane's projection: (half, partner)
+    const int partner = (MU == 0 || MU == 3) ? 2 + half : 3 - half;
+    cdf sa[3], sb[3];
+    load3_df(in, Vh, n, half, sa);
+    load3_df(in, Vh, n, partner, sb);
+    if (g5nb) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sb[c] = {-sb[c].re, -sb[c].im};  // the partner is a lower spin
+    }
+    // projection: hp = s_half + f s_partner with f = +-1 or +-i (the one-thread kernel's
+    // project<MU, FWD> for component `half`)
+    cdf hp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (MU == 0) hp[c] = FWD ? sa[c] + sb[c] : sa[c] - sb[c];
+        else if (MU == 1) hp[c] = FWD ? sa[c] + mul_i(sb[c]) : sa[c] - mul_i(sb[c]);
+        else if (MU == 2) hp[c] = sa[c] + scale_sign(sb[c], FWD == (half == 1));
+        else hp[c] = sa[c] + scale_sign(mul_i(sb[c]), FWD == (half == 1));
+    }
+    // colour: r = V hp (forward, link of x) or V^+ hp (backward, link of the neighbour)
+    const float4* V = FWD ? a.Vdf_out : a.Vdf_in;
+    const int hl = FWD ? h : n;
+    cdf r[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) r[i] = {dfl(0.0), dfl(0.0)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int e = FWD ? i * 3 + j : j * 3 + i;
+            const float4 f = QXD_LDG(V + (size_t)(MU * 9 + e) * Vh + hl);
+            const cdf m = {dfl(f.x, f.y), dfl(f.z, f.w)};
+            if (FWD) cmac(r[i], m, hp[j]);
+            else cmac_conj(r[i], m, hp[j]);
+        }
+    // reconstruction (the one-thread kernel's reconstruct<MU, FWD> for component `half`)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        accO[c] = accO[c] + r[c];
+        if (MU == 0) accP[c] = FWD ? accP[c] + r[c] : accP[c] - r[c];
+        else if (MU == 1) accQ[c] = FWD ? accQ[c] - mul_i(r[c]) : accQ[c] + mul_i(r[c]);
+        else if (MU == 2) accQ[c] = accQ[c] + scale_sign(r[c], FWD == (half == 1));
+        else accP[c] = accP[c] + scale_sign(mul_i(r[c]), FWD == (half == 0));
+    }
+}
+
+template <int SELF, int POST>
+__global__ void __launch_bounds__(kThreads) k_hop_df2(Geo g, HopDev a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int h = t >> 1;
+    const int half = t & 1;
+    const bool live = h < g.Vh;
+    const int hh = live ? h : g.Vh - 1;  // the pair's lanes stay together for the exchange
+    const size_t rhs_off = (size_t)blockIdx.y * 12 * g.Vh;
+    const float4* in = static_cast<const float4*>(a.in_nb) + rhs_off;
+    int x[4];
+    site_coords(g, a.pout, hh, x);
+    cdf accO[3], accP[3], accQ[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) accO[c] = accP[c] = accQ[c] = {dfl(0.0), dfl(0.0)};
+    const bool g5nb = a.g5_nb != 0;
+    hop_half_df<0, true>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<0, false>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<1, true>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<1, false>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<2, true>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<2, false>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<3, true>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    hop_half_df<3, false>(g, a, in, x, hh, half, g5nb, accO, accP, accQ);
+    // exchange: lane 0 takes spins 0 (own accO) and 1 (partner's accO); lane 1 takes
+    // spin 2 = lane0.accP + lane1.accQ and spin 3 = lane0.accQ + lane1.accP
+    cdf pO[3], pP[3], pQ[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        auto sh = [](dfl v) {
+            return dfl(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+        };
+        pO[c] = {sh(accO[c].re), sh(accO[c].im)};
+        pP[c] = {sh(accP[c].re), sh(accP[c].im)};
+        pQ[c] = {sh(accQ[c].re), sh(accQ[c].im)};
+    }
+    if (!live) return;
+    const dfl ch(-0.5 * a.c_hop);
+    cdf v[6];  // this lane's chiral block: spins (2 half, 2 half + 1) x colours
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cdf s0 = half == 0 ? accO[c] : pP[c] + accQ[c];
+        const cdf s1 = half == 0 ? pO[c] : pQ[c] + accP[c];
+        v[c] = {ch * s0.re, ch * s0.im};
+        v[3 + c] = {ch * s1.re, ch * s1.im};
+    }
+    const size_t dstride = (size_t)g.Vh;
+    if constexpr (SELF != 0) {
+        cdf s[6];
+        const float4* self = static_cast<const float4*>(a.in_self) + rhs_off;
+        load3_df(self, g.Vh, h, 2 * half, s);
+        load3_df(self, g.Vh, h, 2 * half + 1, s + 3);
+        if (a.g5_self && half == 1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k] = {-s[k].re, -s[k].im};
+        }
+        if constexpr (SELF == 1) {
+            dfl d[36];
+            const float4* D = static_cast<const float4*>(a.diag) + (size_t)half * 18 * dstride;
+#pragma unroll
+            for (int k = 0; k < 18; ++k) {
+                const float4 f = QXD_LDG(D + (size_t)k * dstride + h);
+                d[2 * k] = dfl(f.x, f.y);
+                d[2 * k + 1] = dfl(f.z, f.w);
+            }
+            cdf o[6];
+            herm6_mul(d, s, o);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) s[k] = o[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = v[k] + s[k];
+    }
+    if constexpr (POST == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = {df_norm(v[k].re), df_norm(v[k].im)};
+        dfl d[36];
+        const float4* D = static_cast<const float4*>(a.diaginv) + (size_t)half * 18 * dstride;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+            const float4 f = QXD_LDG(D + (size_t)k * dstride + h);
+            d[2 * k] = dfl(f.x, f.y);
+            d[2 * k + 1] = dfl(f.z, f.w);
+        }
+        cdf o[6];
+        herm6_mul(d, v, o);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = o[k];
+    }
+    if (a.g5_out && half == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = {-v[k].re, -v[k].im};
+    }
+    float4* out = static_cast<float4*>(a.out) + rhs_off;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const int comp = 6 * half + k;  // complex index 3 spin + colour
+        const dfl re = df_norm(v[k].re), im = df_norm(v[k].im);
+        out[(size_t)comp * g.Vh + h] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    }
+}
+
 // --- host dispatch ---------------------------------------------------------------
 template <int P, int SELF, int POST>
 static void launch_hop_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st, int minb) {
@@ -105,9 +281,25 @@ static void launch_hop_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t s
     }
 }
 
+template <int SELF, int POST>
+static void launch_hop_df2_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st) {
+    dim3 grid(nblocks(2ll * g.Vh), nrhs);
+    k_hop_df2<SELF, POST><<<grid, kThreads, 0, st>>>(g, d);
+}
+
 template <int P>
 static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int nrhs, cudaStream_t st,
                          int minb = 1) {
+    if (P == 3 && minb == 0) {
+        // two threads per site
+        if (self == 0 && post == 0) launch_hop_df2_t<0, 0>(g, d, nrhs, st);
+        else if (self == 0 && post == 1) launch_hop_df2_t<0, 1>(g, d, nrhs, st);
+        else if (self == 1 && post == 0) launch_hop_df2_t<1, 0>(g, d, nrhs, st);
+        else if (self == 1 && post == 1) launch_hop_df2_t<1, 1>(g, d, nrhs, st);
+        else if (self == 2 && post == 0) launch_hop_df2_t<2, 0>(g, d, nrhs, st);
+        else launch_hop_df2_t<2, 1>(g, d, nrhs, st);
+        return;
+    }
     if (self == 0 && post == 0) launch_hop_t<P, 0, 0>(g, d, nrhs, st, minb);
     else if (self == 0 && post == 1) launch_hop_t<P, 0, 1>(g, d, nrhs, st, minb);
     else if (self == 1 && post == 0) launch_hop_t<P, 1, 0>(g, d, nrhs, st, minb);
@@ -116,9 +308,10 @@ static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int 
     else launch_hop_t<P, 2, 1>(g, d, nrhs, st, minb);
 }
 
-// Double-float hop: the launch bound (2, 3 or 4 resident blocks per SM, i.e. up
-// to 255, 168 or 128 registers per thread) is chosen per (mode, nrhs, lattice) by
-// timing the three on the caller's data on first use (the kernel reads its
+// Double-float hop: one thread per site with the launch bound 2, 3 or 4 resident
+// blocks per SM (up to 255, 168 or 128 registers per thread), or two threads per
+// site (k_hop_df2, code 0); chosen per (mode, nrhs, lattice) by timing the four on
+// the caller's data on first use (the kernel reads its
 // inputs and writes a distinct output, so repeating it is harmless); the choice
 // is cached in the context like the multi-right-hand-side shapes.
 static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cudaStream_t st) {
@@ -133,7 +326,7 @@ static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cuda
         QXD_CUDA(ctx, cudaEventCreate(&e0));
         QXD_CUDA(ctx, cudaEventCreate(&e1));
         float best = 1e30f;
-        for (int mb : {2, 3, 4}) {
+        for (int mb : {0, 2, 3, 4}) {
             launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
             QXD_CUDA(ctx, cudaEventRecord(e0, st));
             for (int rep = 0; rep < 3; ++rep) launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);

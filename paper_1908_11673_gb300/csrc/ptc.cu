@@ -793,8 +793,8 @@ int ptc_apply_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int n
 // Loss and gradient over pairs (internal FP32 even fields r[i], e[i]); G accumulated
 // (complex, layout of W).  Returns the summed loss in *loss.
 static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nlayers, int nch, const char* r,
-                                  const char* e, const double* ee, const int* idx, int nb, float2* G, double* loss,
-                                  cudaStream_t st) {
+                                  const char* e, const double* ee, const double* rr, int kind, const int* idx, int nb,
+                                  float2* G, double* loss, cudaStream_t st) {
     const Geo& g = ctx->g;
     const size_t hb = half_bytes(ctx, QXD_FP32);
     const size_t n = 12ull * g.Vh;
@@ -818,16 +818,32 @@ static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nla
         QXD_CUDA(ctx, cudaMemcpyAsync(acts[0], r + (size_t)i * hb, hb, cudaMemcpyDeviceToDevice, st));
         QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(acts[0]) + hb, 0, hb, st));
         QXD_TRY(ptc_forward(ctx, fl, W, nlayers, nch, acts.data(), st));
-        // delta = ((M r)_e - e) / |e|^2 on even sites, 0 on odd sites
         float4* delta = static_cast<float4*>(dA);
-        QXD_CUDA(ctx, cudaMemcpyAsync(delta, acts[nlayers], hb, cudaMemcpyDeviceToDevice, st));
-        QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(delta) + hb, 0, hb, st));
-        QXD_TRY(blas_axpby(ctx, 1, 1, n, -1.0, 0.0, e + (size_t)i * hb, 1.0, 0.0, delta, st));
-        QXD_TRY(blas_norm2(ctx, 1, n, delta, 0, st));
-        QXD_TRY(blas_fetch(ctx, 2, st));
-        if (ctx->red_host[1] != 0.0) return qxd_fail(ctx, QXD_ENAN, "learned preconditioner: non-finite output");
-        tot += ctx->red_host[0] / ee[i];
-        QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, delta, 1.0 / ee[i], 0.0, delta, st));
+        if (kind == 1) {
+            // residual norm: res = Dhat (M r)_e - r; delta = Dhat^+ res / |r|^2 on even sites
+            void *res, *to;
+            QXD_TRY(qxd_ws(ctx, WS_PTC + 14, hb, &res));
+            QXD_TRY(qxd_ws(ctx, WS_PTC + 15, hb, &to));
+            QXD_TRY(op_Dhat(ctx, fl, QXD_FP32, 0, acts[nlayers], res, to, st));
+            QXD_TRY(blas_axpby(ctx, 1, 1, n, -1.0, 0.0, r + (size_t)i * hb, 1.0, 0.0, res, st));
+            QXD_TRY(blas_norm2(ctx, 1, n, res, 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            if (ctx->red_host[1] != 0.0) return qxd_fail(ctx, QXD_ENAN, "learned preconditioner: non-finite output");
+            tot += ctx->red_host[0] / rr[i];
+            QXD_TRY(op_Dhat(ctx, fl, QXD_FP32, 1, res, delta, to, st));
+            QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(delta) + hb, 0, hb, st));
+            QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, delta, 1.0 / rr[i], 0.0, delta, st));
+        } else {
+            // Euclidean error: delta = ((M r)_e - e) / |e|^2 on even sites, 0 on odd sites
+            QXD_CUDA(ctx, cudaMemcpyAsync(delta, acts[nlayers], hb, cudaMemcpyDeviceToDevice, st));
+            QXD_CUDA(ctx, cudaMemsetAsync(reinterpret_cast<char*>(delta) + hb, 0, hb, st));
+            QXD_TRY(blas_axpby(ctx, 1, 1, n, -1.0, 0.0, e + (size_t)i * hb, 1.0, 0.0, delta, st));
+            QXD_TRY(blas_norm2(ctx, 1, n, delta, 0, st));
+            QXD_TRY(blas_fetch(ctx, 2, st));
+            if (ctx->red_host[1] != 0.0) return qxd_fail(ctx, QXD_ENAN, "learned preconditioner: non-finite output");
+            tot += ctx->red_host[0] / ee[i];
+            QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, delta, 1.0 / ee[i], 0.0, delta, st));
+        }
         if (!G) continue;
         float4* dcur = delta;
         float4* dnext = static_cast<float4*>(dB);
@@ -851,7 +867,7 @@ static int ptc_loss_grad_internal(qxd_ctx* ctx, int fl, const float2* W, int nla
 
 // pack canonical complex64 even fields into internal FP32 fields and their norms
 static int pack_pairs(qxd_ctx* ctx, const void* r, const void* e, int npairs, char** R, char** E,
-                      std::vector<double>& ee, cudaStream_t st) {
+                      std::vector<double>& ee, std::vector<double>& rr, cudaStream_t st) {
     const size_t hb = half_bytes(ctx, QXD_FP32);
     const size_t cb = (size_t)ctx->g.Vh * 12 * 8;
     void *dr, *de, *pr, *pe;
@@ -866,13 +882,16 @@ static int pack_pairs(qxd_ctx* ctx, const void* r, const void* e, int npairs, ch
     *R = static_cast<char*>(pr);
     *E = static_cast<char*>(pe);
     ee.resize(npairs);
+    rr.resize(npairs);
     const size_t n = 12ull * ctx->g.Vh;
     for (int i = 0; i < npairs; ++i) {
         QXD_TRY(blas_norm2(ctx, 1, n, *E + (size_t)i * hb, 0, st));
-        QXD_TRY(blas_fetch(ctx, 2, st));
-        if (!(ctx->red_host[0] > 0.0) || ctx->red_host[1] != 0.0)
-            return qxd_fail(ctx, QXD_EARG, "learned preconditioner: error vectors must be finite and non-zero");
+        QXD_TRY(blas_norm2(ctx, 1, n, *R + (size_t)i * hb, 2, st));
+        QXD_TRY(blas_fetch(ctx, 4, st));
+        if (!(ctx->red_host[0] > 0.0) || !(ctx->red_host[2] > 0.0) || ctx->red_host[1] != 0.0 || ctx->red_host[3] != 0.0)
+            return qxd_fail(ctx, QXD_EARG, "learned preconditioner: pair vectors must be finite and non-zero");
         ee[i] = ctx->red_host[0];
+        rr[i] = ctx->red_host[2];
     }
     return QXD_OK;
 }
@@ -953,17 +972,18 @@ int qxd_ptc_apply(qxd_ctx* ctx, int fl, int prec, const float* W, int nlayers, i
 }
 
 int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch, const void* r, const void* e,
-                      int npairs, double* loss, float* grad, void* stream) {
+                      int npairs, int kind, double* loss, float* grad, void* stream) {
     QXD_TRY(ptc_check(ctx, fl));
     QXD_TRY(check_shape(ctx, nlayers, nch));
-    if (!W || !r || !e || npairs < 1 || !loss) return qxd_fail(ctx, QXD_EARG, "ptc_loss_grad: bad arguments");
+    if (!W || !r || !e || npairs < 1 || !loss || (kind != 0 && kind != 1))
+        return qxd_fail(ctx, QXD_EARG, "ptc_loss_grad: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nw = ptc_weight_count(nlayers, nch);
     float2* Wd;
     QXD_TRY(weights_on_device(ctx, W, nw, WS_PTC + 30, &Wd, st));
     char *R, *E;
-    std::vector<double> ee;
-    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, st));
+    std::vector<double> ee, rr;
+    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, rr, st));
     void* G = nullptr;
     if (grad) {
         QXD_TRY(qxd_ws(ctx, WS_PTC + 35, nw * sizeof(float2), &G));
@@ -971,7 +991,7 @@ int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch
     }
     std::vector<int> idx(npairs);
     for (int i = 0; i < npairs; ++i) idx[i] = i;
-    QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), idx.data(), npairs,
+    QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), rr.data(), kind, idx.data(), npairs,
                                    static_cast<float2*>(G), loss, st));
     if (grad) QXD_CUDA(ctx, cudaMemcpyAsync(grad, G, nw * sizeof(float2), cudaMemcpyDefault, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));
@@ -979,10 +999,12 @@ int qxd_ptc_loss_grad(qxd_ctx* ctx, int fl, const float* W, int nlayers, int nch
 }
 
 int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayers, int nch, const void* r,
-                  const void* e, int npairs, int batch, int nsteps, double lr, int* t, double* losses, void* stream) {
+                  const void* e, int npairs, int batch, int nsteps, double lr, int kind, int* t, double* losses,
+                  void* stream) {
     QXD_TRY(ptc_check(ctx, fl));
     QXD_TRY(check_shape(ctx, nlayers, nch));
-    if (!W || !m || !v || !r || !e || !t || npairs < 1 || batch < 1 || nsteps < 0 || !(lr > 0.0))
+    if (!W || !m || !v || !r || !e || !t || npairs < 1 || batch < 1 || nsteps < 0 || !(lr > 0.0) ||
+        (kind != 0 && kind != 1))
         return qxd_fail(ctx, QXD_EARG, "ptc_train: bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nw = ptc_weight_count(nlayers, nch);
@@ -991,8 +1013,8 @@ int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayer
     QXD_TRY(weights_on_device(ctx, m, nw, WS_PTC + 36, &md, st));
     QXD_TRY(weights_on_device(ctx, v, nw, WS_PTC + 37, &vd, st));
     char *R, *E;
-    std::vector<double> ee;
-    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, st));
+    std::vector<double> ee, rr;
+    QXD_TRY(pack_pairs(ctx, r, e, npairs, &R, &E, ee, rr, st));
     void* G;
     QXD_TRY(qxd_ws(ctx, WS_PTC + 35, nw * sizeof(float2), &G));
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -1001,7 +1023,7 @@ int qxd_ptc_train(qxd_ctx* ctx, int fl, float* W, float* m, float* v, int nlayer
         for (int k = 0; k < batch; ++k) idx[k] = (s * batch + k) % npairs;
         QXD_CUDA(ctx, cudaMemsetAsync(G, 0, nw * sizeof(float2), st));
         double L = 0.0;
-        QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), idx.data(), batch,
+        QXD_TRY(ptc_loss_grad_internal(ctx, fl, Wd, nlayers, nch, R, E, ee.data(), rr.data(), kind, idx.data(), batch,
                                        static_cast<float2*>(G), &L, st));
         if (losses) losses[s] = L / batch;
         *t += 1;

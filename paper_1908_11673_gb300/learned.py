@@ -76,14 +76,22 @@ def record(ctx, seed, npairs, stride=None):
     return r, e, lo
 
 
-def train(field, seeds, npairs, epochs=6, batch=10, lr=2e-3, nlayers=4, nch=8, stride=None, device=0):
+def train(field, seeds, npairs, epochs=6, batch=10, lr=2e-3, nlayers=4, nch=8, stride=None, device=0,
+          loss="residual"):
     """Train the network on pairs recorded on the fields of `seeds` (one context
     per field, all on the GPU): Adam from the identity network, `epochs` passes
-    over every field's pairs in batches.  Returns (W, summary) with the mean loss
-    per epoch and the mean loss of the identity, the zero map (1 by definition)
-    and the trained network over all pairs."""
+    over every field's pairs in batches, on the residual-norm loss
+    |r - Dhat M r|^2/|r|^2 (loss="residual", the pair error in the norm |Dhat .|)
+    or the Euclidean error |M r - e|^2/|e|^2 (loss="error").  Returns (W, summary)
+    with the mean loss per epoch and the mean loss of the identity, the zero map
+    (1 by definition) and the trained network over all pairs."""
+    kind = qxd.LOSS_RESIDUAL if loss == "residual" else qxd.LOSS_ERROR
     t0 = time.time()
     W = identity_weights(nlayers, nch)
+    if loss == "residual":
+        # start from M = 2 kappa (the inverse of the mass term of Dhat), the last layer scaled
+        nlast = 16 * 9 * nch  # weights of the last layer (nch -> 1)
+        W[-nlast:] *= np.complex64(2.0 * field["kappa"])
     m = np.zeros_like(W)
     v = np.zeros_like(W)
     t = np.zeros(1, dtype=np.int32)
@@ -98,17 +106,18 @@ def train(field, seeds, npairs, epochs=6, batch=10, lr=2e-3, nlayers=4, nch=8, s
     for _ in range(epochs):
         el = []
         for ctx, r, e in data:
-            el.extend(ctx.ptc_train(0, W, m, v, nlayers, nch, r, e, npairs, batch, steps, lr, t).tolist())
+            el.extend(ctx.ptc_train(0, W, m, v, nlayers, nch, r, e, npairs, batch, steps, lr, t, kind=kind).tolist())
         history.append(float(np.mean(el)))
     t_train = time.time() - t0 - t_pairs
     ident = identity_weights(nlayers, nch)
-    loss_id = float(np.mean([ctx.ptc_loss_grad(0, ident, nlayers, nch, r, e, npairs) / npairs
+    loss_id = float(np.mean([ctx.ptc_loss_grad(0, ident, nlayers, nch, r, e, npairs, kind=kind) / npairs
                              for ctx, r, e in data]))
-    loss_tr = float(np.mean([ctx.ptc_loss_grad(0, W, nlayers, nch, r, e, npairs) / npairs for ctx, r, e in data]))
+    loss_tr = float(np.mean([ctx.ptc_loss_grad(0, W, nlayers, nch, r, e, npairs, kind=kind) / npairs
+                             for ctx, r, e in data]))
     for ctx, _, _ in data:
         ctx.close()
     return W, {"fields": len(seeds), "pairs": len(seeds) * npairs, "network": f"{nlayers} layers x {nch} channels",
-               "epochs": epochs, "loss_zero_map": 1.0, "loss_identity": loss_id, "loss_trained": loss_tr,
+               "loss": loss, "epochs": epochs, "loss_zero_map": 1.0, "loss_identity": loss_id, "loss_trained": loss_tr,
                "loss_history": history, "seconds_pairs": t_pairs, "seconds_training": t_train}
 
 
@@ -157,12 +166,13 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--nlayers", type=int, default=4)
     ap.add_argument("--nch", type=int, default=8)
+    ap.add_argument("--loss", choices=["residual", "error"], default="residual")
     ap.add_argument("--out", default=None, help="write the JSON summary here")
     ap.add_argument("--weights", default=None, help="save the trained weights (.npy)")
     args = ap.parse_args(argv)
 
     W, summ_train = train(FIELD, [4000 + i for i in range(args.train_fields)], args.pairs, args.epochs, args.batch,
-                          args.lr, args.nlayers, args.nch)
+                          args.lr, args.nlayers, args.nch, loss=args.loss)
     evals = []
     for i in range(args.eval_fields):
         ctx = make_context(4100 + i)

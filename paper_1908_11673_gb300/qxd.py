@@ -20,6 +20,7 @@ FP64, FP32, BF16 = 0, 1, 2
 CGNE, FGCR, MSCG = 0, 1, 2
 PRECOND_NONE, PRECOND_LEARNED, PRECOND_SAP, PRECOND_DFL = 0, 1, 2, 3
 TBC_PERIODIC, TBC_OPEN = 0, 1
+LOSS_ERROR, LOSS_RESIDUAL = 0, 1
 
 STATUS = {0: "QXD_OK", 1: "QXD_EARG", 2: "QXD_ENOCONV", 3: "QXD_EBREAKDOWN", 4: "QXD_ENAN",
           5: "QXD_ECUDA", 6: "QXD_ENOMEM", 7: "QXD_ESTATE"}
@@ -110,8 +111,8 @@ def load_library(path: str = LIBPATH) -> ctypes.CDLL:
         "qxd_set_sap": (i, [vp, i, i]),
         "qxd_sap_apply": (i, [vp, i, vp, vp, vp]),
         "qxd_ptc_apply": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
-        "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, ctypes.POINTER(d), vp, vp]),
-        "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, ctypes.POINTER(i), vp, vp]),
+        "qxd_ptc_loss_grad": (i, [vp, i, vp, i, i, vp, vp, i, i, ctypes.POINTER(d), vp, vp]),
+        "qxd_ptc_train": (i, [vp, i, vp, vp, vp, i, i, vp, vp, i, i, i, d, i, ctypes.POINTER(i), vp, vp]),
         "qxd_ptc_record_pairs": (i, [vp, i, vp, i, i, vp, vp, vp]),
         "qxd_rat_apply": (i, [vp, i, ctypes.POINTER(Rational), i, i, ctypes.POINTER(Solver), vp, vp,
                               ctypes.POINTER(Info), vp]),
@@ -371,19 +372,21 @@ class Context:
         self._check(self.lib.qxd_ptc_apply(self._h, int(fl), int(prec), _ptr(W), int(nlayers), int(nch), _ptr(inp),
                                            _ptr(out), _stream(stream)))
 
-    def ptc_loss_grad(self, fl, W, nlayers, nch, r, e, npairs, grad=None, stream=None):
+    def ptc_loss_grad(self, fl, W, nlayers, nch, r, e, npairs, grad=None, stream=None, kind=LOSS_ERROR):
+        """Summed loss over the pairs (kind LOSS_ERROR or LOSS_RESIDUAL) and its gradient."""
         loss = ctypes.c_double()
         self._check(self.lib.qxd_ptc_loss_grad(self._h, int(fl), _ptr(W), int(nlayers), int(nch), _ptr(r), _ptr(e),
-                                               int(npairs), ctypes.byref(loss), _ptr(grad), _stream(stream)))
+                                               int(npairs), int(kind), ctypes.byref(loss), _ptr(grad),
+                                               _stream(stream)))
         return loss.value
 
-    def ptc_train(self, fl, W, m, v, nlayers, nch, r, e, npairs, batch, nsteps, lr, t, stream=None):
+    def ptc_train(self, fl, W, m, v, nlayers, nch, r, e, npairs, batch, nsteps, lr, t, stream=None, kind=LOSS_ERROR):
         """Adam steps on (W, m, v) in place; t is a one-element int32 array (step counter).
         Returns the per-step mean losses."""
         losses = np.zeros(max(nsteps, 1), dtype=np.float64)
         tc = ctypes.c_int(int(t[0]))
         self._check(self.lib.qxd_ptc_train(self._h, int(fl), _ptr(W), _ptr(m), _ptr(v), int(nlayers), int(nch),
-                                           _ptr(r), _ptr(e), int(npairs), int(batch), int(nsteps), float(lr),
+                                           _ptr(r), _ptr(e), int(npairs), int(batch), int(nsteps), float(lr), int(kind),
                                            ctypes.byref(tc), losses.ctypes.data, _stream(stream)))
         t[0] = tc.value
         return losses[:nsteps]

@@ -67,7 +67,8 @@ def test_forward_parity(L, cstar, theta, nch):
 
 @pytest.mark.parametrize("L,cstar,theta", GEOMS)
 @pytest.mark.parametrize("nch", [3, 12])
-def test_loss_and_gradient_parity(L, cstar, theta, nch):
+@pytest.mark.parametrize("norm", ["error", "residual"])
+def test_loss_and_gradient_parity(L, cstar, theta, nch, norm):
     qxd, ctx, op, _, _ = setup(L, cstar, theta, qhat=-2, seed=7200)
     nl = 3
     Ws = rand_weights(np.random.default_rng(2), nl, nch)
@@ -76,10 +77,11 @@ def test_loss_and_gradient_parity(L, cstar, theta, nch):
     e = workload.spinor(ne, 7202, nrhs=2).astype(np.complex64)
     W32 = flat(Ws)
     grad = np.zeros_like(W32)
-    loss = ctx.ptc_loss_grad(0, W32, nl, nch, r, e, 2, grad=grad)
+    kind = qxd.LOSS_RESIDUAL if norm == "residual" else qxd.LOSS_ERROR
+    loss = ctx.ptc_loss_grad(0, W32, nl, nch, r, e, 2, grad=grad, kind=kind)
     Wr = unflat(W32.astype(np.complex128), nl, nch)
     pairs = [(r[i].astype(np.complex128), e[i].astype(np.complex128)) for i in range(2)]
-    L0, G = ptc.loss_and_grad(ptc.Transport(op), Wr, pairs)
+    L0, G = ptc.loss_and_grad(ptc.Transport(op), Wr, pairs, norm=norm)
     assert abs(loss - L0) <= 1e-5 * L0
     assert relerr(grad.astype(np.complex128), np.concatenate([g.reshape(-1) for g in G])) <= 1e-4
     ctx.close()
