@@ -362,11 +362,11 @@ def spectral_range(ctx, qxd, torch, dev, stream, V, n_power=40, n_inverse=5):
             "inside_printed_range": bool(lam_max <= rb * rb and lam_min >= ra * ra)}
 
 
-def precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, solve_kw, V):
-    """SAP(5,5)-, SAP(3,4)- and DFL+SAP(3,4)-preconditioned FGCR (Sec. 4.4) on the
+def precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, solve_kw, V, sap=((5, 5), (3, 4))):
+    """SAP(ncy,nmr)- and DFL+SAP(3,4)-preconditioned FGCR (Sec. 4.4) on the
     context's system, each timed with CUDA events (one solve after a warm-up)."""
     nxt = {}
-    for ncy, nmr in ((5, 5), (3, 4)):
+    for ncy, nmr in sap:
         ctx.set_sap(ncy, nmr)
         ctx.solve(0, eta_d, psi_d, **(solve_kw | {"precond": qxd.PRECOND_SAP, "nkv": 16}))
         ctx.profile(2)
@@ -401,8 +401,7 @@ def precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, solve_kw, V)
 def rough_row(args, qxd, torch, dev, stream, timed, fp32_kw):
     """The bench lattice and couplings on rougher synthetic fields (plaquette about
     0.63 after smearing, the value the configurations aim at): plain FP64 CGNE,
-    the unpreconditioned mixed FGCR, SAP and DFL+SAP, and the mixed 4-RHS learned
-    batch, to 1e-10 each."""
+    the unpreconditioned mixed FGCR, SAP(3,4) and DFL+SAP(3,4), to 1e-10 each."""
     from paper_1908_11673_gb300 import workload
     w = WORKLOADS["32^3x64-cstar3-rough"]
     U, A, eta = make_inputs(w, str(dev))
@@ -420,9 +419,8 @@ def rough_row(args, qxd, torch, dev, stream, timed, fp32_kw):
     row["fgcr_mixed"] = {"ms": ms, "iters": inf[0].iters, "true_relres": inf[0].true_relres}
     ms64, inf64 = timed(lambda: ctx.solve(0, eta_d, psi_d, kind=qxd.CGNE, tol=1e-10, nmx=200000, stream=stream), 1)
     row["fp64_cgne"] = {"ms": ms64, "iters": inf64[0].iters, "true_relres": inf64[0].true_relres}
-    row.update(precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, fp32_kw, V))
+    row.update(precond_rows(ctx, qxd, torch, dev, stream, timed, eta_d, psi_d, fp32_kw, V, sap=((3, 4),)))
     del eta_d, psi_d
-    row["learned_batched_mixed"] = learned_row(ctx, qxd, torch, dev, stream, timed, w, V, ms64)
     ctx.close()
     return row
 

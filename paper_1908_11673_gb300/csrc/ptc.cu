@@ -331,8 +331,8 @@ __global__ void k_ptc_wgrad_final(const float2* __restrict__ partials, int nblk,
 //   out_i[site][(c,s)] = sum_d sum_{(c',s')} W[c][c'][d][s][s'] (T_d a_{c'})_i[site][s'],
 // written over the reals ([Re, Im] of the transports times the 2 x 2 real form of
 // each complex weight): M = 128 sites of a tile, N = 2*4*COUTP, K = 2*4*CINP per
-// direction d.  A CTA of 256 threads forms the transports of one direction for its
-// tile (thread = site and half of the input channels), rounds them to bfloat16 into
+// direction d.  A CTA of 512 threads forms the transports of one direction for its
+// tile (thread = site and a pair of input channels), rounds them to bfloat16 into
 // shared memory in the canonical K-major layout (8-row x 16-byte core matrices),
 // and one thread issues the tcgen05.mma instructions for the three colour rows,
 // accumulating in FP32 in tensor memory (three N-column accumulators), while the
@@ -343,7 +343,7 @@ __global__ void k_ptc_wgrad_final(const float2* __restrict__ partials, int nblk,
 // for all tiles of the persistent CTA.  Every wait on an mbarrier is bounded: on a
 // time-out the CTA flags the error, writes NaN to its tile, releases its tensor
 // memory and returns.
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcRows = 128;      // sites per tile (MMA M)
 constexpr int kTcTmemCols = 256;  // three accumulators of up to 64 columns
 constexpr unsigned kTcSpin = 1u << 20;
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     constexpr uint32_t idesc = tc_idesc(kTcRows, N);
     uint32_t phase[2] = {0u, 0u};
     const int row = tid % kTcRows;
-    const int half = tid / kTcRows;  // input channels 4 half .. 4 half + 3
+    const int quarter = tid / kTcRows;  // input channels 2 quarter, 2 quarter + 1
     const int tiles = (g.Vh + kTcRows - 1) / kTcRows;
     bool failed = false;
     for (int tile = blockIdx.x; tile < 2 * tiles && !failed; tile += gridDim.x) {
@@ -548,12 +548,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             PtcLink lk;
             if (live && d > 0) link_for(g, L, d, p, h, x, lk);
-            if (CINP == 2) {
-                if (half == 0) tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 0, row, Abuf[b]);
-            } else {
-                tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 4 * half, row, Abuf[b]);
-                tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 4 * half + 2, row, Abuf[b]);
-            }
+            if (CINP == 8 || quarter == 0)
+                tc_produce_pair<CINP>(g, d, p, h, live, lk, a, cin, 2 * quarter, row, Abuf[b]);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (tid == 0) {
@@ -581,13 +577,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // epilogue: warp w reads lanes 32 (w % 4) ..; warps 0-3 colours 0 and 1, warps 4-7 colour 2
+        // epilogue: warp w reads lanes 32 (w % 4) ..; warps 4i .. 4i + 3 colour row i
         const int warp = tid >> 5, lane = tid & 31;
         const int q = warp & 3;
         const int site = 32 * q + lane;
         const int hs = (tile % tiles) * kTcRows + site;
         const size_t chs = (size_t)12 * g.Vh;
-        for (int i = (warp < 4 ? 0 : 2); i < (warp < 4 ? 2 : 3); ++i) {
+        const int i = warp >> 2;  // warps 12-15 have no colour row to read
+        if (i < 3) {
             float v[N];
 #pragma unroll
             for (int c16 = 0; c16 < N / 16; ++c16)
@@ -620,7 +617,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const int tiles_ = (g.Vh + kTcRows - 1) / kTcRows;
         const int p = blockIdx.x / tiles_;
         const int hs = (blockIdx.x % tiles_) * kTcRows + row;
-        if (half == 0 && p < 2 && hs < g.Vh) {
+        if (quarter == 0 && p < 2 && hs < g.Vh) {
             const size_t chs = (size_t)12 * g.Vh;
             for (int c = 0; c < ng; ++c)
                 for (int k = 0; k < 6; ++k)

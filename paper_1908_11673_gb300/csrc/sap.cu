@@ -171,32 +171,15 @@ __device__ __forceinline__ void hop_sap(const Geo& g, const SapDev& a, const Sap
     for (int k = 0; k < 12; ++k) out[k] = -0.5f * out[k];
 }
 
-// L2 policy for the site-diagonal terms: a sweep reads a block's terms once per
-// minimal-residual step, so they are marked to stay in L2 (evict_last) while the
-// single-use data of the sweep (links, source, solution) passes through
-__device__ __forceinline__ uint64_t l2_keep_policy() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ float4 ldg_keep(const float4* ptr, uint64_t pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(ptr), "l"(pol));
-    return v;
-}
-
-// s = D s for a packed site-diagonal term (two Hermitian 6x6 blocks), read from
-// global memory (kept in L2) one block at a time
+// s = D s for a packed site-diagonal term (two Hermitian 6x6 blocks), streamed
+// from global memory one block at a time
 __device__ __forceinline__ void diag_mul(const float4* __restrict__ D, int Vh, int h, cplx<float> s[12]) {
-    const uint64_t pol = l2_keep_policy();
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
         float d[36];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            const float4 v = ldg_keep(D + (size_t)(blk * 9 + k) * Vh + h, pol);
+            const float4 v = QXD_LDG(D + (size_t)(blk * 9 + k) * Vh + h);
             d[4 * k] = v.x;
             d[4 * k + 1] = v.y;
             d[4 * k + 2] = v.z;
