@@ -12,8 +12,11 @@
 // number of blocks, so that blocks of one colour never touch, across the
 // periodic boundary included.
 //
-// GPU layout: one launch per colour sweep, one CTA per block, 128 threads; thread
-// t owns the t-th even and the t-th odd site of the block.  The block's links are
+// GPU layout: one launch per colour sweep, one CTA per block, 256 threads; the lane
+// pair (2u, 2u + 1) owns the u-th even and the u-th odd site of the block, lane h
+// the chiral block (spins 2h, 2h + 1) of every field, so that a lane keeps half a
+// spinor per field and applies one 6 x 6 block of the site-diagonal terms (128
+// registers, two CTAs and 16 warps per SM).  The block's links are
 // staged in shared memory once per sweep, so the 2 nmr + 2 block hops of the
 // minimal-residual steps read links and neighbour spinors from shared memory only.
 // The sweep also computes the block residual rho = eta - D psi itself (the
@@ -33,6 +36,7 @@ namespace qxd {
 constexpr int kSapB = kBlk;
 constexpr int kSapThreads = kBlkThreads;
 constexpr int kSapSites = kBlkSites;
+constexpr int kSapLanes = 2 * kSapThreads;  // threads of a sweep CTA: two lanes per (even, odd) site pair
 
 struct SapDev {
     int nb[4];              // blocks per direction
@@ -51,22 +55,55 @@ struct SapShared {
     float2 lk[4][7][kSapSites];      // U rows 0, 1 (6 complex) and z^qhat, per direction and local site
     float2 sp[2][12][kSapThreads];   // spinor buffers by parity
     float2 rho_o[12][kSapThreads];   // residual on the odd sites
-    float red[3 * kSapThreads / 32];
+    float red[3 * kSapLanes / 32];
 };
 
-__device__ __forceinline__ void load_sm(const float2 (*sm)[kSapThreads], int t, cplx<float> s[12]) {
+// A pair of adjacent lanes (2u, 2u + 1) owns the u-th even and the u-th odd site
+// of the block; lane `half` holds the spins 2 half, 2 half + 1 (its chiral block,
+// complex components 6 half .. 6 half + 5) of every field it keeps.
+__device__ __forceinline__ void load6_sm(const float2 (*sm)[kSapThreads], int u, int half, cplx<float> v[6]) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-        const float2 v = sm[k][t];
-        s[k] = {v.x, v.y};
+    for (int k = 0; k < 6; ++k) {
+        const float2 x = sm[6 * half + k][u];
+        v[k] = {x.x, x.y};
     }
 }
-__device__ __forceinline__ void store_sm(float2 (*sm)[kSapThreads], int t, const cplx<float> s[12]) {
+__device__ __forceinline__ void store6_sm(float2 (*sm)[kSapThreads], int u, int half, const cplx<float> v[6]) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) sm[k][t] = make_float2(s[k].re, s[k].im);
+    for (int k = 0; k < 6; ++k) sm[6 * half + k][u] = make_float2(v[k].re, v[k].im);
+}
+// the chiral block of a global FP32 field: complex 6 half + k is in chunk 3 half + k / 2
+__device__ __forceinline__ void load6_glob(const float4* __restrict__ b, int Vh, int h, int half, cplx<float> v[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float4 f = QXD_LDG(b + (size_t)(3 * half + c) * Vh + h);
+        v[2 * c] = {f.x, f.y};
+        v[2 * c + 1] = {f.z, f.w};
+    }
+}
+__device__ __forceinline__ void store6_glob(float4* __restrict__ b, int Vh, int h, int half, const cplx<float> v[6]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        b[(size_t)(3 * half + c) * Vh + h] = make_float4(v[2 * c].re, v[2 * c].im, v[2 * c + 1].re, v[2 * c + 1].im);
+}
+// spin sp (three colours) of a site
+__device__ __forceinline__ void load_spin_sm(const float2 (*sm)[kSapThreads], int u, int sp, cplx<float> v[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float2 x = sm[3 * sp + c][u];
+        v[c] = {x.x, x.y};
+    }
+}
+__device__ __forceinline__ void load_spin_glob(const float4* __restrict__ b, int Vh, int h, int sp, cplx<float> v[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int k = 3 * sp + c;
+        const float4 f = QXD_LDG(b + (size_t)(k >> 1) * Vh + h);
+        v[c] = (k & 1) ? cplx<float>{f.z, f.w} : cplx<float>{f.x, f.y};
+    }
 }
 
-// link of direction mu at the block's local site sid (= parity * 128 + thread) from shared memory
+// link of direction mu at the block's local site sid (= parity * 128 + slot) from shared memory
 __device__ __forceinline__ void link_sm(const SapShared& S, int mu, int sid, Mat3<float>& m, cplx<float>& z) {
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -84,57 +121,24 @@ __device__ __forceinline__ void link_sm(const SapShared& S, int mu, int sid, Mat
     z = {zz.x, zz.y};
 }
 
-__device__ __forceinline__ void phase_mul(cplx<float> z, bool dag, Half<float>& o) {
-#pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o.a[sp][c] = dag ? cmul_conj(z, o.a[sp][c]) : z * o.a[sp][c];
-}
-
-// acc += hop terms of direction MU at site s (parity p) from the opposite-parity
-// spinor buffer nb.  HALO = false: hops leaving the block are dropped (block
-// operator).  HALO = true: they take the spinor of the neighbouring site from the
-// global field nb_glob (opposite parity) and, backwards, its link from global memory.
-// spin projection / reconstruction for the hop d = 2 mu + (0 forward, 1 backward),
-// chosen at run time
-__device__ __forceinline__ void project_rt(int d, const cplx<float> v[12], Half<float>& hp) {
-    switch (d) {
-        case 0: project<0, true>(v, hp); break;
-        case 1: project<0, false>(v, hp); break;
-        case 2: project<1, true>(v, hp); break;
-        case 3: project<1, false>(v, hp); break;
-        case 4: project<2, true>(v, hp); break;
-        case 5: project<2, false>(v, hp); break;
-        case 6: project<3, true>(v, hp); break;
-        default: project<3, false>(v, hp); break;
-    }
-}
-__device__ __forceinline__ void reconstruct_rt(int d, const Half<float>& o, cplx<float> acc[12]) {
-    switch (d) {
-        case 0: reconstruct<0, true>(o, acc); break;
-        case 1: reconstruct<0, false>(o, acc); break;
-        case 2: reconstruct<1, true>(o, acc); break;
-        case 3: reconstruct<1, false>(o, acc); break;
-        case 4: reconstruct<2, true>(o, acc); break;
-        case 5: reconstruct<2, false>(o, acc); break;
-        case 6: reconstruct<3, true>(o, acc); break;
-        default: reconstruct<3, false>(o, acc); break;
-    }
-}
-
-// out = -1/2 sum_mu [(1 - gamma_mu) V(x,mu) f(x+mu) + (1 + gamma_mu) V(x-mu,mu)^+ f(x-mu)]
-// at site s of parity p, f the opposite-parity spinors in the buffer nb.
-// HALO = false: hops leaving the block are dropped (block operator).  HALO = true:
-// they take the spinor of the neighbouring site from the global field nb_glob
-// (opposite parity) and, backwards, its link from global memory.
-// The eight hops run as one loop with the direction chosen at run time, so the
-// colour multiplication exists once in the code: the sweep calls this six times,
-// and fully unrolled copies overflow the instruction cache.
+// This lane's chiral block of
+//   out = -1/2 sum_mu [(1 - gamma_mu) V(x,mu) f(x+mu) + (1 + gamma_mu) V(x-mu,mu)^+ f(x-mu)]
+// at site s of parity p, f the opposite-parity spinors in the buffer nb.  HALO = false:
+// hops leaving the block are dropped (block operator); HALO = true: they take the
+// spinor of the neighbouring site from the global field nb_glob and, backwards, its
+// link from global memory.  Lane `half` forms the half-spinor component `half` of
+// each projection (spins half and its partner), multiplies it by the link and adds it
+// into spin half (accO) and into the lower spin it feeds (accP = spin 2 + half for
+// directions 0, 3; accQ = spin 3 - half for directions 1, 2); the two lanes then
+// exchange their partial sums.  The eight hops run as one loop with run-time signs,
+// so the colour multiplication exists once in the code.
 template <bool HALO>
-__device__ __forceinline__ void hop_sap(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
-                                        const float2 (*nb)[kSapThreads], const float4* nb_glob, cplx<float> out[12]) {
+__device__ __forceinline__ void hop_pair(const Geo& g, const SapDev& a, const SapShared& S, const SiteRef& s, int p,
+                                         const float2 (*nb)[kSapThreads], const float4* nb_glob, int half,
+                                         cplx<float> out[6]) {
+    cplx<float> accO[3], accP[3], accQ[3];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = {0.f, 0.f};
+    for (int c = 0; c < 3; ++c) accO[c] = accP[c] = accQ[c] = {0.f, 0.f};
     const int t = block_thread(s.l);
     const int sid = p * kSapThreads + t;
 #pragma unroll 1
@@ -144,52 +148,91 @@ __device__ __forceinline__ void hop_sap(const Geo& g, const SapDev& a, const Sap
         const int lmu = mu == 0 ? s.l[0] : mu == 1 ? s.l[1] : mu == 2 ? s.l[2] : s.l[3];
         const bool inside = fwd ? lmu + 1 < kSapB : lmu > 0;
         if (!inside && !HALO) continue;
-        cplx<float> v[12];
+        const int partner = (mu == 0 || mu == 3) ? 2 + half : 3 - half;
+        cplx<float> sa[3], sb[3];
         Mat3<float> m;
         cplx<float> z;
         if (inside) {
-            // thread index of the neighbour within its parity
             const int l3 = s.l[3];
             const int step = mu == 0 ? 32 : mu == 1 ? 8 : mu == 2 ? 2 : 0;
             const int tn = mu < 3 ? (fwd ? t + step : t - step) : (fwd ? t + (l3 & 1) : t - ((l3 & 1) ^ 1));
-            load_sm(nb, tn, v);
+            load_spin_sm(nb, tn, half, sa);
+            load_spin_sm(nb, tn, partner, sb);
             link_sm(S, mu, fwd ? sid : (1 - p) * kSapThreads + tn, m, z);
         } else {
             const int hn = neighbour_lex(g, s.x, mu, fwd ? +1 : -1) >> 1;
-            load_spinor<1>(nb_glob, g.Vh, hn, v);
+            load_spin_glob(nb_glob, g.Vh, hn, half, sa);
+            load_spin_glob(nb_glob, g.Vh, hn, partner, sb);
             if (fwd) link_sm(S, mu, sid, m, z);
             else load_link32(a.U32[1 - p], a.Z32[1 - p], g.Vh, mu, hn, m, z);
         }
-        Half<float> hp, o;
-        project_rt(d, v, hp);
-        if (fwd) mul_half<false>(m, hp, o);
-        else mul_half<true>(m, hp, o);
-        phase_mul(z, !fwd, o);
-        reconstruct_rt(d, o, out);
+        // projection (1 -+ gamma_mu), component `half`: s_half + f s_partner, f = +-1 or +-i
+        const bool imag = (mu & 1) != 0;
+        const bool negp = mu < 2 ? !fwd : (fwd == (half == 1));
+        cplx<float> hp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const cplx<float> tb = imag ? times_i(sb[c]) : sb[c];
+            hp[c] = negp ? sa[c] - tb : sa[c] + tb;
+        }
+        // colour: V hp forwards, V^+ hp backwards; then the U(1) phase
+        cplx<float> r[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            cplx<float> acc = {0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (fwd) cmac(acc, m.a[i][j], hp[j]);
+                else cmac_conj(acc, m.a[j][i], hp[j]);
+            }
+            r[i] = fwd ? z * acc : cmul_conj(z, acc);
+        }
+        // reconstruction: spin half gets r, the lower spin it feeds +-r or +-i r
+        const bool negr = mu == 0 ? !fwd : mu == 1 ? fwd : mu == 2 ? (fwd == (half == 1)) : (fwd == (half == 0));
+        const bool to_p = mu == 0 || mu == 3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            accO[c] = accO[c] + r[c];
+            cplx<float> dl = imag ? times_i(r[c]) : r[c];
+            if (negr) dl = -dl;
+            if (to_p) accP[c] = accP[c] + dl;
+            else accQ[c] = accQ[c] + dl;
+        }
+    }
+    // lane 0 takes spins 0 (own accO) and 1 (partner's accO); lane 1 spin 2 (lane 0's
+    // accP + own accQ) and spin 3 (lane 0's accQ + own accP)
+    cplx<float> pO[3], pP[3], pQ[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        pO[c] = {__shfl_xor_sync(0xffffffffu, accO[c].re, 1), __shfl_xor_sync(0xffffffffu, accO[c].im, 1)};
+        pP[c] = {__shfl_xor_sync(0xffffffffu, accP[c].re, 1), __shfl_xor_sync(0xffffffffu, accP[c].im, 1)};
+        pQ[c] = {__shfl_xor_sync(0xffffffffu, accQ[c].re, 1), __shfl_xor_sync(0xffffffffu, accQ[c].im, 1)};
     }
 #pragma unroll
-    for (int k = 0; k < 12; ++k) out[k] = -0.5f * out[k];
+    for (int c = 0; c < 3; ++c) {
+        const cplx<float> s0 = half == 0 ? accO[c] : pP[c] + accQ[c];
+        const cplx<float> s1 = half == 0 ? pO[c] : pQ[c] + accP[c];
+        out[c] = -0.5f * s0;
+        out[3 + c] = -0.5f * s1;
+    }
 }
 
-// s = D s for a packed site-diagonal term (two Hermitian 6x6 blocks), streamed
-// from global memory one block at a time
-__device__ __forceinline__ void diag_mul(const float4* __restrict__ D, int Vh, int h, cplx<float> s[12]) {
+// v = D v for this lane's chiral block of a packed site-diagonal term (one
+// Hermitian 6x6 block, 9 float4), streamed from global memory
+__device__ __forceinline__ void diag6(const float4* __restrict__ D, int Vh, int h, int half, cplx<float> v[6]) {
+    float d[36];
 #pragma unroll
-    for (int blk = 0; blk < 2; ++blk) {
-        float d[36];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const float4 v = QXD_LDG(D + (size_t)(blk * 9 + k) * Vh + h);
-            d[4 * k] = v.x;
-            d[4 * k + 1] = v.y;
-            d[4 * k + 2] = v.z;
-            d[4 * k + 3] = v.w;
-        }
-        cplx<float> o[6];
-        herm6_mul(d, s + 6 * blk, o);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) s[6 * blk + i] = o[i];
+    for (int k = 0; k < 9; ++k) {
+        const float4 f = QXD_LDG(D + (size_t)(half * 9 + k) * Vh + h);
+        d[4 * k] = f.x;
+        d[4 * k + 1] = f.y;
+        d[4 * k + 2] = f.z;
+        d[4 * k + 3] = f.w;
     }
+    cplx<float> o[6];
+    herm6_mul(d, v, o);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v[i] = o[i];
 }
 
 // sum over the CTA of three floats
@@ -204,7 +247,7 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* sh) {
     __syncthreads();
     for (int k = 0; k < 3; ++k) {
         float s = 0.f;
-        for (int w = 0; w < kSapThreads / 32; ++w) s += sh[w * 3 + k];
+        for (int w = 0; w < kSapLanes / 32; ++w) s += sh[w * 3 + k];
         v[k] = s;
     }
     __syncthreads();
@@ -215,26 +258,28 @@ __device__ __forceinline__ void cta_sum3(float v[3], float* sh) {
 // Dirichlet block system approximately by nmr minimal-residual steps on the
 // block's even-odd system, and adds the block solution to psi.  Blocks of one
 // colour never touch, so every CTA reads the other colour's psi on its halo
-// and writes its own sites only.
+// and writes its own sites only.  Two lanes per site pair (one chiral block each).
 template <bool FIRST>
-__global__ void __launch_bounds__(kSapThreads) k_sap_sweep(Geo g, SapDev a, int colour) {
+__global__ void __launch_bounds__(kSapLanes, 2) k_sap_sweep(Geo g, SapDev a, int colour) {
     extern __shared__ __align__(16) unsigned char sap_smem[];
     SapShared& S = *reinterpret_cast<SapShared*>(sap_smem);
     int bc[4];
     block_coords(blockIdx.x, a.nb, bc);
     if (((bc[0] + bc[1] + bc[2] + bc[3]) & 1) != colour) return;
-    const int t = threadIdx.x;
+    const int u = threadIdx.x >> 1;
+    const int half = threadIdx.x & 1;
     const int Vh = g.Vh;
     SiteRef se, so;
-    block_site(g, bc, 0, t, se);
-    block_site(g, bc, 1, t, so);
-    // the block's links into shared memory (this thread: its even and its odd site)
+    block_site(g, bc, 0, u, se);
+    block_site(g, bc, 1, u, so);
+    // the block's links into shared memory: lane `half` stages directions 2 half, 2 half + 1
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int h = p == 0 ? se.h : so.h;
-        const int sid = p * kSapThreads + t;
+        const int sid = p * kSapThreads + u;
 #pragma unroll
-        for (int mu = 0; mu < 4; ++mu) {
+        for (int q = 0; q < 2; ++q) {
+            const int mu = 2 * half + q;
             const float4 c0 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 0) * Vh + h);
             const float4 c1 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 1) * Vh + h);
             const float4 c2 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 2) * Vh + h);
@@ -245,101 +290,98 @@ __global__ void __launch_bounds__(kSapThreads) k_sap_sweep(Geo g, SapDev a, int 
             S.lk[mu][4][sid] = make_float2(c2.x, c2.y);
             S.lk[mu][5][sid] = make_float2(c2.z, c2.w);
         }
-        const float4 z01 = QXD_LDG(a.Z32[p] + h);
-        const float4 z23 = QXD_LDG(a.Z32[p] + (size_t)Vh + h);
-        S.lk[0][6][sid] = make_float2(z01.x, z01.y);
-        S.lk[1][6][sid] = make_float2(z01.z, z01.w);
-        S.lk[2][6][sid] = make_float2(z23.x, z23.y);
-        S.lk[3][6][sid] = make_float2(z23.z, z23.w);
+        const float4 zz = QXD_LDG(a.Z32[p] + (size_t)half * Vh + h);
+        S.lk[2 * half][6][sid] = make_float2(zz.x, zz.y);
+        S.lk[2 * half + 1][6][sid] = make_float2(zz.z, zz.w);
     }
     const float4* psi_e = a.psi;
     const float4* psi_o = a.psi + 6 * (size_t)Vh;
-    cplx<float> v[12], r[12], y[12], p[12];
+    cplx<float> v[6], r[6], y[6], pv[6];
     // residual rho = eta - D psi on the block's sites: r (even), rho_o (odd, shared)
-    load_spinor<1>(a.eta, Vh, se.h, r);
-    load_spinor<1>(a.eta + 6 * (size_t)Vh, Vh, so.h, y);
+    load6_glob(a.eta, Vh, se.h, half, r);
+    load6_glob(a.eta + 6 * (size_t)Vh, Vh, so.h, half, y);
     if (!FIRST) {
-        load_spinor<1>(psi_e, Vh, se.h, v);
-        store_sm(S.sp[0], t, v);
-        load_spinor<1>(psi_o, Vh, so.h, p);
-        store_sm(S.sp[1], t, p);
+        load6_glob(psi_e, Vh, se.h, half, v);
+        store6_sm(S.sp[0], u, half, v);
+        load6_glob(psi_o, Vh, so.h, half, pv);
+        store6_sm(S.sp[1], u, half, pv);
         __syncthreads();
         // even site: A_ee psi_e + H_eo psi_o
-        diag_mul(a.A[0], Vh, se.h, v);
+        diag6(a.A[0], Vh, se.h, half, v);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) r[k] = r[k] - v[k];
-        hop_sap<true>(g, a, S, se, 0, S.sp[1], psi_o, v);
+        for (int k = 0; k < 6; ++k) r[k] = r[k] - v[k];
+        hop_pair<true>(g, a, S, se, 0, S.sp[1], psi_o, half, v);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) r[k] = r[k] - v[k];
+        for (int k = 0; k < 6; ++k) r[k] = r[k] - v[k];
         // odd site: A_oo psi_o + H_oe psi_e
-        diag_mul(a.A[1], Vh, so.h, p);
+        diag6(a.A[1], Vh, so.h, half, pv);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) y[k] = y[k] - p[k];
-        hop_sap<true>(g, a, S, so, 1, S.sp[0], psi_e, v);
+        for (int k = 0; k < 6; ++k) y[k] = y[k] - pv[k];
+        hop_pair<true>(g, a, S, so, 1, S.sp[0], psi_e, half, v);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) y[k] = y[k] - v[k];
+        for (int k = 0; k < 6; ++k) y[k] = y[k] - v[k];
     }
-    store_sm(S.rho_o, t, y);
+    store6_sm(S.rho_o, u, half, y);
     // t_o = A_oo^-1 rho_o;  b_e = rho_e - H^B_eo t_o
-    diag_mul(a.Aoo_inv, Vh, so.h, y);
-    __syncthreads();  // every thread is done with the psi buffers
-    store_sm(S.sp[1], t, y);
+    diag6(a.Aoo_inv, Vh, so.h, half, y);
+    __syncthreads();  // every lane is done with the psi buffers
+    store6_sm(S.sp[1], u, half, y);
     __syncthreads();
-    hop_sap<false>(g, a, S, se, 0, S.sp[1], nullptr, v);
+    hop_pair<false>(g, a, S, se, 0, S.sp[1], nullptr, half, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < 6; ++k) {
         r[k] = r[k] - v[k];
         y[k] = {0.f, 0.f};
     }
-    store_sm(S.sp[0], t, r);
+    store6_sm(S.sp[0], u, half, r);
     __syncthreads();
     for (int it = 0; it < a.nmr; ++it) {
         // t_o = A_oo^-1 H^B_oe r_e
-        hop_sap<false>(g, a, S, so, 1, S.sp[0], nullptr, v);
-        diag_mul(a.Aoo_inv, Vh, so.h, v);
-        store_sm(S.sp[1], t, v);
+        hop_pair<false>(g, a, S, so, 1, S.sp[0], nullptr, half, v);
+        diag6(a.Aoo_inv, Vh, so.h, half, v);
+        store6_sm(S.sp[1], u, half, v);
         __syncthreads();
         // p = Dhat_B r = A_ee r - H^B_eo t_o
-        hop_sap<false>(g, a, S, se, 0, S.sp[1], nullptr, v);
+        hop_pair<false>(g, a, S, se, 0, S.sp[1], nullptr, half, v);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) p[k] = r[k];
-        diag_mul(a.A[0], Vh, se.h, p);
+        for (int k = 0; k < 6; ++k) pv[k] = r[k];
+        diag6(a.A[0], Vh, se.h, half, pv);
         float s3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            p[k] = p[k] - v[k];
-            s3[0] += p[k].re * r[k].re + p[k].im * r[k].im;  // <p, r> = sum conj(p) r
-            s3[1] += p[k].re * r[k].im - p[k].im * r[k].re;
-            s3[2] += p[k].re * p[k].re + p[k].im * p[k].im;
+        for (int k = 0; k < 6; ++k) {
+            pv[k] = pv[k] - v[k];
+            s3[0] += pv[k].re * r[k].re + pv[k].im * r[k].im;  // <p, r> = sum conj(p) r
+            s3[1] += pv[k].re * r[k].im - pv[k].im * r[k].re;
+            s3[2] += pv[k].re * pv[k].re + pv[k].im * pv[k].im;
         }
         cta_sum3(s3, S.red);
         const cplx<float> alpha = s3[2] > 0.f ? cplx<float>{s3[0] / s3[2], s3[1] / s3[2]} : cplx<float>{0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
+        for (int k = 0; k < 6; ++k) {
             cmac(y[k], alpha, r[k]);
-            r[k] = r[k] - alpha * p[k];
+            r[k] = r[k] - alpha * pv[k];
         }
-        store_sm(S.sp[0], t, r);
+        store6_sm(S.sp[0], u, half, r);
         __syncthreads();
     }
     // d_o = A_oo^-1 (rho_o - H^B_oe y);  psi += d
-    store_sm(S.sp[0], t, y);
+    store6_sm(S.sp[0], u, half, y);
     __syncthreads();
-    hop_sap<false>(g, a, S, so, 1, S.sp[0], nullptr, v);
-    load_sm(S.rho_o, t, p);
+    hop_pair<false>(g, a, S, so, 1, S.sp[0], nullptr, half, v);
+    load6_sm(S.rho_o, u, half, pv);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = p[k] - v[k];
-    diag_mul(a.Aoo_inv, Vh, so.h, v);
+    for (int k = 0; k < 6; ++k) v[k] = pv[k] - v[k];
+    diag6(a.Aoo_inv, Vh, so.h, half, v);
     if (!FIRST) {
-        load_spinor<1>(psi_e, Vh, se.h, p);
+        load6_glob(psi_e, Vh, se.h, half, pv);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) y[k] = y[k] + p[k];
-        load_spinor<1>(psi_o, Vh, so.h, p);
+        for (int k = 0; k < 6; ++k) y[k] = y[k] + pv[k];
+        load6_glob(psi_o, Vh, so.h, half, pv);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = v[k] + p[k];
+        for (int k = 0; k < 6; ++k) v[k] = v[k] + pv[k];
     }
-    store_spinor<1>(a.psi, Vh, se.h, y);
-    store_spinor<1>(a.psi + 6 * (size_t)Vh, Vh, so.h, v);
+    store6_glob(a.psi, Vh, se.h, half, y);
+    store6_glob(a.psi + 6 * (size_t)Vh, Vh, so.h, half, v);
 }
 
 int sap_check(qxd_ctx* ctx) {
@@ -381,9 +423,9 @@ int sap_apply_full(qxd_ctx* ctx, int fl, const float4* eta, float4* psi, cudaStr
         for (int colour = 0; colour < 2; ++colour) {
             ProfScope prof(ctx, "sap_sweep", (double)g.Vh * site_bytes, st);
             if (cy == 0 && colour == 0)
-                k_sap_sweep<true><<<nblk, kSapThreads, smem, st>>>(g, a, colour);
+                k_sap_sweep<true><<<nblk, kSapLanes, smem, st>>>(g, a, colour);
             else
-                k_sap_sweep<false><<<nblk, kSapThreads, smem, st>>>(g, a, colour);
+                k_sap_sweep<false><<<nblk, kSapLanes, smem, st>>>(g, a, colour);
             QXD_CUDA(ctx, cudaGetLastError());
         }
     }
