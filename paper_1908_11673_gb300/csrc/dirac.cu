@@ -167,8 +167,8 @@ __device__ __forceinline__ void hop_half_df(const Geo& g, const HopDev& a, const
     }
 }
 
-template <int SELF, int POST>
-__global__ void __launch_bounds__(kThreads) k_hop_df2(Geo g, HopDev a) {
+template <int SELF, int POST, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_hop_df2(Geo g, HopDev a) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int h = t >> 1;
     const int half = t & 1;
@@ -282,24 +282,27 @@ static void launch_hop_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t s
 }
 
 template <int SELF, int POST>
-static void launch_hop_df2_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st) {
+static void launch_hop_df2_t(const Geo& g, const HopDev& d, int nrhs, cudaStream_t st, int minb) {
     dim3 grid(nblocks(2ll * g.Vh), nrhs);
-    k_hop_df2<SELF, POST><<<grid, kThreads, 0, st>>>(g, d);
+    if (minb == 5) k_hop_df2<SELF, POST, 5><<<grid, kThreads, 0, st>>>(g, d);
+    else k_hop_df2<SELF, POST, 4><<<grid, kThreads, 0, st>>>(g, d);
+}
+
+// the double-float operators use two modes: D_w (self 1, post 0) and the first half
+// of Dhat (self 0, post 1); only these are compiled
+static void launch_hop_df(const Geo& g, const HopDev& d, int self, int post, int nrhs, cudaStream_t st, int minb) {
+    if (minb < 0) {  // two threads per site, launch bound -minb CTAs per SM
+        if (self == 1) launch_hop_df2_t<1, 0>(g, d, nrhs, st, -minb);
+        else launch_hop_df2_t<0, 1>(g, d, nrhs, st, -minb);
+    } else {
+        if (self == 1) launch_hop_t<3, 1, 0>(g, d, nrhs, st, minb);
+        else launch_hop_t<3, 0, 1>(g, d, nrhs, st, minb);
+    }
 }
 
 template <int P>
 static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int nrhs, cudaStream_t st,
                          int minb = 1) {
-    if (P == 3 && minb == 0) {
-        // two threads per site
-        if (self == 0 && post == 0) launch_hop_df2_t<0, 0>(g, d, nrhs, st);
-        else if (self == 0 && post == 1) launch_hop_df2_t<0, 1>(g, d, nrhs, st);
-        else if (self == 1 && post == 0) launch_hop_df2_t<1, 0>(g, d, nrhs, st);
-        else if (self == 1 && post == 1) launch_hop_df2_t<1, 1>(g, d, nrhs, st);
-        else if (self == 2 && post == 0) launch_hop_df2_t<2, 0>(g, d, nrhs, st);
-        else launch_hop_df2_t<2, 1>(g, d, nrhs, st);
-        return;
-    }
     if (self == 0 && post == 0) launch_hop_t<P, 0, 0>(g, d, nrhs, st, minb);
     else if (self == 0 && post == 1) launch_hop_t<P, 0, 1>(g, d, nrhs, st, minb);
     else if (self == 1 && post == 0) launch_hop_t<P, 1, 0>(g, d, nrhs, st, minb);
@@ -309,13 +312,15 @@ static void launch_hop_p(const Geo& g, const HopDev& d, int self, int post, int 
 }
 
 // Double-float hop: one thread per site with the launch bound 2, 3 or 4 resident
-// blocks per SM (up to 255, 168 or 128 registers per thread), or two threads per
-// site (k_hop_df2, code 0); chosen per (mode, nrhs, lattice) by timing the four on
-// the caller's data on first use (the kernel reads its
+// blocks per SM (up to 255, 168 or 128 registers per thread; codes 2, 3, 4), or two
+// threads per site (k_hop_df2) with 4 or 5 (128 or 96 registers; codes -4, -5);
+// chosen per (mode, nrhs, lattice) by timing the five on the caller's data on first use (the kernel reads its
 // inputs and writes a distinct output, so repeating it is harmless); the choice
 // is cached in the context like the multi-right-hand-side shapes.
 static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cudaStream_t st) {
     const Geo& g = ctx->g;
+    if (!((a.self_mode == 1 && a.post_mode == 0) || (a.self_mode == 0 && a.post_mode == 1)))
+        return qxd_fail(ctx, QXD_EARG, "double-float hop: only D_w and the first half of Dhat are compiled");
     const auto key = std::make_tuple((int)QXD_DF64, a.self_mode, a.post_mode, a.nrhs, (long long)g.Vh);
     auto it = ctx->tune_hop.find(key);
     int minb = 4;
@@ -326,10 +331,10 @@ static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cuda
         QXD_CUDA(ctx, cudaEventCreate(&e0));
         QXD_CUDA(ctx, cudaEventCreate(&e1));
         float best = 1e30f;
-        for (int mb : {0, 2, 3, 4}) {
-            launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
+        for (int mb : {-4, -5, 2, 3, 4}) {
+            launch_hop_df(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
             QXD_CUDA(ctx, cudaEventRecord(e0, st));
-            for (int rep = 0; rep < 3; ++rep) launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
+            for (int rep = 0; rep < 3; ++rep) launch_hop_df(g, d, a.self_mode, a.post_mode, a.nrhs, st, mb);
             QXD_CUDA(ctx, cudaEventRecord(e1, st));
             QXD_CUDA(ctx, cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -343,7 +348,7 @@ static int launch_hop_df64(qxd_ctx* ctx, const HopDev& d, const HopArgs& a, cuda
         cudaEventDestroy(e1);
         ctx->tune_hop.emplace(key, std::make_pair(minb, kThreads));
     }
-    launch_hop_p<3>(g, d, a.self_mode, a.post_mode, a.nrhs, st, minb);
+    launch_hop_df(g, d, a.self_mode, a.post_mode, a.nrhs, st, minb);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }
