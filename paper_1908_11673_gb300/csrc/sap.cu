@@ -72,34 +72,11 @@ __device__ __forceinline__ void store6_sm(float2 (*sm)[kSapThreads], int u, int 
 #pragma unroll
     for (int k = 0; k < 6; ++k) sm[6 * half + k][u] = make_float2(v[k].re, v[k].im);
 }
-// L2 policy of the site-diagonal terms: a sweep reads a block's terms once per
-// minimal-residual step (A_ee nmr + 1 times, A_oo^-1 nmr + 2 times), so they are
-// marked to stay in L2 (evict_last) while the single-use data of the sweep (the block's
-// links, source and solution) is marked evict_first; ldg_keep takes either policy
-__device__ __forceinline__ uint64_t l2_keep_policy() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ uint64_t l2_stream_policy() {
-    uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
-    return p;
-}
-__device__ __forceinline__ float4 ldg_keep(const float4* ptr, uint64_t pol) {
-    float4 v;
-    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(ptr), "l"(pol));
-    return v;
-}
-
 // the chiral block of a global FP32 field: complex 6 half + k is in chunk 3 half + k / 2
 __device__ __forceinline__ void load6_glob(const float4* __restrict__ b, int Vh, int h, int half, cplx<float> v[6]) {
-    const uint64_t pol = l2_stream_policy();
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const float4 f = ldg_keep(b + (size_t)(3 * half + c) * Vh + h, pol);
+        const float4 f = QXD_LDG(b + (size_t)(3 * half + c) * Vh + h);
         v[2 * c] = {f.x, f.y};
         v[2 * c + 1] = {f.z, f.w};
     }
@@ -241,13 +218,12 @@ __device__ __forceinline__ void hop_pair(const Geo& g, const SapDev& a, const Sa
 }
 
 // v = D v for this lane's chiral block of a packed site-diagonal term (one
-// Hermitian 6x6 block, 9 float4), read from global memory (kept in L2)
+// Hermitian 6x6 block, 9 float4), streamed from global memory
 __device__ __forceinline__ void diag6(const float4* __restrict__ D, int Vh, int h, int half, cplx<float> v[6]) {
-    const uint64_t pol = l2_keep_policy();
     float d[36];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const float4 f = ldg_keep(D + (size_t)(half * 9 + k) * Vh + h, pol);
+        const float4 f = QXD_LDG(D + (size_t)(half * 9 + k) * Vh + h);
         d[4 * k] = f.x;
         d[4 * k + 1] = f.y;
         d[4 * k + 2] = f.z;
@@ -297,7 +273,6 @@ __global__ void __launch_bounds__(kSapLanes, 2) k_sap_sweep(Geo g, SapDev a, int
     block_site(g, bc, 0, u, se);
     block_site(g, bc, 1, u, so);
     // the block's links into shared memory: lane `half` stages directions 2 half, 2 half + 1
-    const uint64_t stream_pol = l2_stream_policy();
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int h = p == 0 ? se.h : so.h;
@@ -305,9 +280,9 @@ __global__ void __launch_bounds__(kSapLanes, 2) k_sap_sweep(Geo g, SapDev a, int
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int mu = 2 * half + q;
-            const float4 c0 = ldg_keep(a.U32[p] + (size_t)(mu * 3 + 0) * Vh + h, stream_pol);
-            const float4 c1 = ldg_keep(a.U32[p] + (size_t)(mu * 3 + 1) * Vh + h, stream_pol);
-            const float4 c2 = ldg_keep(a.U32[p] + (size_t)(mu * 3 + 2) * Vh + h, stream_pol);
+            const float4 c0 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 0) * Vh + h);
+            const float4 c1 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 1) * Vh + h);
+            const float4 c2 = QXD_LDG(a.U32[p] + (size_t)(mu * 3 + 2) * Vh + h);
             S.lk[mu][0][sid] = make_float2(c0.x, c0.y);
             S.lk[mu][1][sid] = make_float2(c0.z, c0.w);
             S.lk[mu][2][sid] = make_float2(c1.x, c1.y);
