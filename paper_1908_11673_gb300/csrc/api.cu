@@ -167,6 +167,7 @@ static void free_flavour(QxdFlavour& F) {
     cudaFree(F.dfl_basis);
     cudaFree(F.dfl_A);
     cudaFree(F.dfl_nbr);
+    cudaFree(F.dfl_stat);
     F = QxdFlavour{};
 }
 
@@ -273,13 +274,7 @@ int qxd_set_clover(qxd_ctx* ctx, int fl, const qxd_flavour* f, void* stream) {
     cudaFree(F.Cdf[1]);
     F.Vdf = nullptr;
     F.Cdf[0] = F.Cdf[1] = nullptr;
-    cudaFree(F.dfl_basis);
-    cudaFree(F.dfl_A);
-    cudaFree(F.dfl_nbr);
-    F.dfl_basis = nullptr;
-    F.dfl_A = nullptr;
-    F.dfl_nbr = nullptr;
-    F.dfl_Ns = 0;
+    dfl_free(F);
     QXD_TRY(launch_set_flavour(ctx, fl, st));
     F.set = true;
     return QXD_OK;
@@ -395,6 +390,7 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
         QXD_TRY(launch_unpack(ctx, QXD_FP64, bxo, 1, 0, dout, 1, nrhs, st));
         QXD_TRY(finish_out(ctx, psi, dout, cbytes, host_out, st));
         QXD_CUDA(ctx, cudaStreamSynchronize(st));
+        if (s->precond == QXD_PRECOND_DFL) QXD_TRY(dfl_status(ctx, fl, nullptr, nullptr, st));
         return rc;
     }
     for (int r = 0; r < nrhs; ++r) {
@@ -420,6 +416,7 @@ int qxd_solve(qxd_ctx* ctx, int fl, const qxd_solver* s, const void* eta, void* 
     }
     QXD_TRY(finish_out(ctx, psi, dout, cbytes, host_out, st));
     QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    if (s->precond == QXD_PRECOND_DFL) QXD_TRY(dfl_status(ctx, fl, nullptr, nullptr, st));
     return worst;
 }
 

@@ -17,6 +17,7 @@
 // warp reads consecutive entries when it forms row k of A x.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "blas.h"
@@ -253,24 +254,358 @@ __global__ void __launch_bounds__(kBlkThreads) k_dfl_little(Geo g, DflGrid G, Df
     }
 }
 
-// y = A x on the block grid: one warp per block, lane k forms row k
-__global__ void k_dfl_coarse(DflGrid G, int Ns, const int* __restrict__ nbr, const float2* __restrict__ A,
-                             const float2* __restrict__ x, float2* __restrict__ y) {
-    const int B = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int k = threadIdx.x & 31;
-    if (B >= G.Nb || k >= Ns) return;
-    cplx<float> acc = {0.f, 0.f};
-    for (int s = 0; s < 9; ++s) {
-        const float2* As = A + ((size_t)B * 9 + s) * Ns * Ns;
-        const float2* xs = x + (size_t)__ldg(nbr + B * 9 + s) * Ns;
-        for (int l = 0; l < Ns; ++l) {
-            const float2 a = __ldg(As + (size_t)l * Ns + k);
-            const float2 xv = __ldg(xs + l);
-            acc.re += a.x * xv.x - a.y * xv.y;
-            acc.im += a.x * xv.y + a.y * xv.x;
+// ---- little-system solver: restarted GCR on the block grid in one cooperative launch ----
+//
+// A x = b (FP32 vectors [Nb][Ns], sums in FP64), x from zero, restarted every nkv steps, until
+// |b - A x| <= tol |b| or nmx steps.  Step k of a cycle, with w_j, p_j (j < k) the orthonormal
+// directions of the cycle and r orthogonal to every w_j:
+//   phase 1  w = A r; partial sums of c_j = <w_j, w>, |w|^2 and <w, r>       (barrier)
+//   phase 2  |w'|^2 = |w|^2 - sum_j |c_j|^2 for w' = w - sum_j c_j w_j, and <w', r> = <w, r>;
+//            w_k = w' / |w'|, p_k = (r - sum_j c_j p_j) / |w'|, alpha = <w_k, r>,
+//            x += alpha p_k, r -= alpha w_k; partial sums of |r|^2            (barrier)
+// When |w'|^2 < cancel |w|^2 (cancellation; cancel = 0.01) w' and its products are formed
+// explicitly first, with one more barrier.  Every CTA reduces the per-CTA partial sums itself, in the same
+// order, so that all CTAs take the same decisions.  The grid barrier polls with a limit; a
+// CTA that gives up records the error and leaves, and the others then give up at their next
+// barrier.
+constexpr int kCgThreads = 512;
+constexpr int kCgWarps = kCgThreads / 32;
+constexpr int kCgMaxK = 32;                // restart length bound
+constexpr int kCgPart = 68;                // doubles per CTA and partial-sum region
+constexpr long long kCgSpin = 1ll << 22;   // barrier polls before giving up
+
+struct CgBar {
+    unsigned count, gen;
+    int err, pad;
+};
+struct CgStat {
+    int iters, err;
+    double relres;
+};
+struct CgArgs {
+    DflGrid G;
+    int Ns, nkv, nmx;
+    double tol2;
+    double cancel;  // explicit norm when |w'|^2 < cancel |w|^2
+    const int* nbr;
+    const float2* A;
+    const float2* b;
+    float2* x;
+    float2* r;
+    float2* P;  // [nkv][Nb * Ns]
+    float2* W;  // [nkv][Nb * Ns]
+    double* part;  // [3][gridDim.x][kCgPart]
+    CgBar* bar;
+    CgStat* stat;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// grid-wide barrier; false if this CTA gave up waiting or another CTA did before
+__device__ bool cg_sync(CgBar* b) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int good = 1;
+        const unsigned g = ld_acquire_gpu(&b->gen);
+        __threadfence();
+        if (atomicAdd(&b->count, 1u) == gridDim.x - 1) {
+            atomicExch(&b->count, 0u);
+            __threadfence();
+            atomicAdd(&b->gen, 1u);
+        } else {
+            long long polls = 0;
+            while (ld_acquire_gpu(&b->gen) == g) {
+                if (++polls > kCgSpin) {
+                    atomicExch(&b->err, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (*reinterpret_cast<volatile int*>(&b->err)) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// FP64 sum of v over the CTA (the same order on every CTA); every thread gets it
+__device__ double cg_cta_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < kCgWarps; ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
+
+// out[c] = sum over CTAs i = 0, 1, ... of part[i][c], into shared memory (tmp: kCgThreads
+// doubles), for ncol columns: c = 0 .. split - 1 and 64, 65, ... after them (split = ncol:
+// the first ncol); the same thread mapping and order on every CTA
+__device__ void cg_reduce(const double* part, int ncol, int split, double* out, double* tmp) {
+    const int q = min(kCgThreads / ncol, 32);
+    const int t = threadIdx.x, cc = t % ncol, grp = t / ncol;
+    const int c = cc < split ? cc : 64 + cc - split;
+    if (grp < q) {
+        double s = 0.0;
+#pragma unroll 4
+        for (int i = grp; i < (int)gridDim.x; i += q) s += part[(size_t)i * kCgPart + c];
+        tmp[grp * ncol + cc] = s;
+    }
+    __syncthreads();
+    if (t < ncol) {
+        double s = 0.0;
+        for (int g = 0; g < q; ++g) s += tmp[g * ncol + t];
+        out[c] = s;
+    }
+    __syncthreads();
+}
+
+// one halving step of the warp transpose-sum: M entries -> M/2, lanes with bit O set keep the
+// upper half
+template <int M, int O>
+__device__ __forceinline__ void halve(float (&v)[2 * kCgMaxK]) {
+    const bool up = (threadIdx.x & O) != 0;
+#pragma unroll
+    for (int i = 0; i < M / 2; ++i) {
+        const float send = up ? v[i] : v[i + M / 2];
+        const float keep = up ? v[i + M / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+    }
+}
+
+// phase 1: w = A r into W[k]; partial sums of <W_j, w> (j < k), |w|^2 and <w, r> -> part.
+// A warp takes blocks B = B0, B0 + S, ...: for each, its lanes stage the nine neighbour
+// blocks' entries of r in shared memory (xs, 9 Ns per warp), then lane (grp, col) forms row
+// col of A r over the rows l = grp (mod ng) of the nine Ns x Ns blocks, three rows (27 loads)
+// at a time.  The sums then run over the warp's entries with all 32 lanes.
+__device__ void cg_phase1(const CgArgs& a, int k, float* sred, float2* xs) {
+    const int Ns = a.Ns;
+    const size_t n = (size_t)a.G.Nb * Ns;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ng = 32 / Ns;  // rows of A handled side by side
+    const int grp = lane / Ns, col = lane - grp * Ns;
+    const float2* r = a.r;
+    const int B0 = blockIdx.x * kCgWarps + warp, S = gridDim.x * kCgWarps;
+    for (int B = B0; B < a.G.Nb; B += S) {
+        for (int i = lane; i < 9 * Ns; i += 32) {
+            const int sl = i / Ns;
+            xs[i] = r[(size_t)__ldg(a.nbr + (size_t)B * 9 + sl) * Ns + (i - sl * Ns)];
+        }
+        __syncwarp();
+        float ar = 0.f, ai = 0.f;
+        if (grp < ng) {
+            const float2* AB = a.A + (size_t)B * 9 * Ns * Ns + col;
+            for (int l0 = grp; l0 < Ns; l0 += 3 * ng) {
+                float2 av[3][9];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int l = l0 + u * ng;
+#pragma unroll
+                    for (int sl = 0; sl < 9; ++sl)
+                        av[u][sl] = l < Ns ? __ldg(AB + ((size_t)sl * Ns + l) * Ns) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int l = min(l0 + u * ng, Ns - 1);  // av is zero past the last row
+#pragma unroll
+                    for (int sl = 0; sl < 9; ++sl) {
+                        const float2 xv = xs[sl * Ns + l];
+                        ar += av[u][sl].x * xv.x - av[u][sl].y * xv.y;
+                        ai += av[u][sl].x * xv.y + av[u][sl].y * xv.x;
+                    }
+                }
+            }
+        }
+        const float ar0 = ar, ai0 = ai;
+        for (int g = 1; g < ng; ++g) {
+            ar += __shfl_sync(0xffffffffu, ar0, lane + g * Ns);
+            ai += __shfl_sync(0xffffffffu, ai0, lane + g * Ns);
+        }
+        if (lane < Ns) a.W[(size_t)k * n + (size_t)B * Ns + lane] = make_float2(ar, ai);
+        __syncwarp();  // xs reused; W[k] entries read by other lanes below
+    }
+    float v[2 * kCgMaxK];
+#pragma unroll
+    for (int j = 0; j < 2 * kCgMaxK; ++j) v[j] = 0.f;
+    float ww = 0.f, wrr = 0.f, wri = 0.f;
+    const int nbw = B0 < a.G.Nb ? (a.G.Nb - B0 + S - 1) / S : 0;  // blocks of this warp
+    for (int f = lane; f < nbw * Ns; f += 32) {
+        const int i = f / Ns;
+        const size_t e = (size_t)(B0 + i * S) * Ns + (f - i * Ns);
+        const float2 w = a.W[(size_t)k * n + e];
+        const float2 rv = r[e];
+        ww += w.x * w.x + w.y * w.y;
+        wrr += w.x * rv.x + w.y * rv.y;  // <w, r> = conj(w) r
+        wri += w.x * rv.y - w.y * rv.x;
+#pragma unroll
+        for (int j = 0; j < kCgMaxK; ++j)
+            if (j < k) {
+                const float2 wj = a.W[(size_t)j * n + e];
+                v[2 * j] += wj.x * w.x + wj.y * w.y;  // <W_j, w>
+                v[2 * j + 1] += wj.x * w.y - wj.y * w.x;
+            }
+    }
+    halve<64, 16>(v);
+    halve<32, 8>(v);
+    halve<16, 4>(v);
+    halve<8, 2>(v);
+    halve<4, 1>(v);  // lane l now holds the warp totals of <W_l, w> in v[0], v[1]
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ww += __shfl_xor_sync(0xffffffffu, ww, o);
+        wrr += __shfl_xor_sync(0xffffffffu, wrr, o);
+        wri += __shfl_xor_sync(0xffffffffu, wri, o);
+    }
+    sred[warp * kCgPart + 2 * lane] = v[0];
+    sred[warp * kCgPart + 2 * lane + 1] = v[1];
+    if (lane == 0) {
+        sred[warp * kCgPart + 64] = ww;
+        sred[warp * kCgPart + 65] = wrr;
+        sred[warp * kCgPart + 66] = wri;
+    }
+    __syncthreads();
+    if (threadIdx.x < 67) {
+        double s = 0.0;
+        for (int w = 0; w < kCgWarps; ++w) s += (double)sred[w * kCgPart + threadIdx.x];
+        a.part[(size_t)blockIdx.x * kCgPart + threadIdx.x] = s;
+    }
+}
+
+// phase 2 over every entry e: w = (W_k - sum_{j < nj} c_j W_j) inv, p = (src - sum_{j < nj} c_j P_j) inv;
+// with update: W_k = w, P_k = p, x += alpha p, r -= alpha w, and the CTA's |r|^2 into part;
+// without: W_k = w, P_k = p, and the CTA's |w|^2 and <w, r> into part
+__device__ void cg_phase2(const CgArgs& a, int k, int nj, const float2* cf, float inv, float2 alpha,
+                          const float2* src, bool update, double* part, double* shd) {
+    const size_t n = (size_t)a.G.Nb * a.Ns;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    for (size_t e = (size_t)blockIdx.x * kCgThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kCgThreads) {
+        float2 w = a.W[(size_t)k * n + e];
+        float2 p = src[e];
+#pragma unroll 4
+        for (int j = 0; j < nj; ++j) {
+            const float2 c = cf[j], wj = a.W[(size_t)j * n + e], pj = a.P[(size_t)j * n + e];
+            w.x -= c.x * wj.x - c.y * wj.y;
+            w.y -= c.x * wj.y + c.y * wj.x;
+            p.x -= c.x * pj.x - c.y * pj.y;
+            p.y -= c.x * pj.y + c.y * pj.x;
+        }
+        w = make_float2(w.x * inv, w.y * inv);
+        p = make_float2(p.x * inv, p.y * inv);
+        a.W[(size_t)k * n + e] = w;
+        a.P[(size_t)k * n + e] = p;
+        float2 rv = a.r[e];
+        if (update) {
+            float2 xv = a.x[e];
+            xv.x += alpha.x * p.x - alpha.y * p.y;
+            xv.y += alpha.x * p.y + alpha.y * p.x;
+            rv.x -= alpha.x * w.x - alpha.y * w.y;
+            rv.y -= alpha.x * w.y + alpha.y * w.x;
+            a.x[e] = xv;
+            a.r[e] = rv;
+            s0 += rv.x * rv.x + rv.y * rv.y;
+        } else {
+            s0 += w.x * w.x + w.y * w.y;
+            s1 += w.x * rv.x + w.y * rv.y;
+            s2 += w.x * rv.y - w.y * rv.x;
         }
     }
-    y[(size_t)B * Ns + k] = make_float2(acc.re, acc.im);
+    const double t0 = cg_cta_sum(s0, shd);
+    if (update) {
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * kCgPart] = t0;
+        return;
+    }
+    const double t1 = cg_cta_sum(s1, shd), t2 = cg_cta_sum(s2, shd);
+    if (threadIdx.x == 0) {
+        part[(size_t)blockIdx.x * kCgPart] = t0;
+        part[(size_t)blockIdx.x * kCgPart + 1] = t1;
+        part[(size_t)blockIdx.x * kCgPart + 2] = t2;
+    }
+}
+
+__global__ void __launch_bounds__(kCgThreads, 1) k_dfl_gcr(CgArgs a) {
+    __shared__ float sred[kCgWarps * kCgPart];
+    __shared__ float2 xs[kCgWarps * 9 * kCgMaxK];
+    __shared__ double red[kCgPart], tmp[kCgThreads];
+    __shared__ double shd[kCgWarps];
+    __shared__ float2 cf[kCgMaxK];
+    __shared__ float coef[4];  // inv, alpha.re, alpha.im, mode
+    const size_t n = (size_t)a.G.Nb * a.Ns;
+    double* part0 = a.part;                                // phase 1 sums
+    double* part1 = a.part + (size_t)gridDim.x * kCgPart;  // |r|^2
+    double* part2 = part1 + (size_t)gridDim.x * kCgPart;   // explicit |w'|^2, <w', r>
+    // x = 0, r = b, |b|^2
+    float s = 0.f;
+    for (size_t e = (size_t)blockIdx.x * kCgThreads + threadIdx.x; e < n; e += (size_t)gridDim.x * kCgThreads) {
+        const float2 bv = a.b[e];
+        a.r[e] = bv;
+        a.x[e] = make_float2(0.f, 0.f);
+        s += bv.x * bv.x + bv.y * bv.y;
+    }
+    const double bs = cg_cta_sum(s, shd);
+    if (threadIdx.x == 0) part1[(size_t)blockIdx.x * kCgPart] = bs;
+    int it = 0;
+    double bb = 0.0, rr = 0.0;
+    bool ok = cg_sync(a.bar);
+    if (ok) {
+        cg_reduce(part1, 1, 1, red, tmp);
+        bb = rr = red[0];
+    }
+    for (int k = 0; ok && bb > 0.0 && it < a.nmx && rr > a.tol2 * bb; k = (k + 1 == a.nkv) ? 0 : k + 1) {
+        cg_phase1(a, k, sred, xs + (threadIdx.x >> 5) * 9 * kCgMaxK);
+        if (!(ok = cg_sync(a.bar))) break;
+        cg_reduce(part0, 2 * k + 3, 2 * k, red, tmp);
+        if (threadIdx.x == 0) {
+            const double ww = red[64];
+            double cc = 0.0;
+            for (int j = 0; j < k; ++j) {
+                cc += red[2 * j] * red[2 * j] + red[2 * j + 1] * red[2 * j + 1];
+                cf[j] = make_float2((float)red[2 * j], (float)red[2 * j + 1]);
+            }
+            const double w2 = ww - cc;
+            int mode = 0;  // 0: implicit norm, 1: explicit, 2: breakdown
+            if (!(ww > 0.0) || !isfinite(ww)) mode = 2;
+            else if (!(w2 >= a.cancel * ww)) mode = 1;
+            const double inv = mode == 0 ? 1.0 / sqrt(w2) : 1.0;
+            coef[0] = (float)inv;
+            coef[1] = (float)(red[65] * inv);
+            coef[2] = (float)(red[66] * inv);
+            coef[3] = (float)mode;
+        }
+        __syncthreads();
+        const int mode = (int)coef[3];
+        if (mode == 2) break;
+        if (mode == 1) {
+            cg_phase2(a, k, k, cf, 1.f, make_float2(0.f, 0.f), a.r, false, part2, shd);
+            if (!(ok = cg_sync(a.bar))) break;
+            cg_reduce(part2, 3, 3, red, tmp);
+            if (!(red[0] > 0.0) || !isfinite(red[0])) break;
+            const double inv = 1.0 / sqrt(red[0]);
+            cg_phase2(a, k, 0, cf, (float)inv, make_float2((float)(red[1] * inv), (float)(red[2] * inv)),
+                      a.P + (size_t)k * n, true, part1, shd);
+        } else {
+            cg_phase2(a, k, k, cf, coef[0], make_float2(coef[1], coef[2]), a.r, true, part1, shd);
+        }
+        if (!(ok = cg_sync(a.bar))) break;
+        cg_reduce(part1, 1, 1, red, tmp);
+        rr = red[0];
+        ++it;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.stat->iters = it;
+        a.stat->relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    if (threadIdx.x == 0 && !ok) atomicExch(&a.stat->err, 1);
 }
 
 DflGrid dfl_grid(const Geo& g) {
@@ -374,101 +709,69 @@ int assemble_little(qxd_ctx* ctx, int fl, QxdFlavour& F, cudaStream_t st) {
     return QXD_OK;
 }
 
-int coarse_apply(qxd_ctx* ctx, const QxdFlavour& F, const float2* x, float2* y, cudaStream_t st) {
+// A^-1 b to a relative residual ctol (restarted GCR, one cooperative launch); the step
+// count, residual and barrier status go to F.dfl_stat
+int coarse_gcr(qxd_ctx* ctx, const QxdFlavour& F, const float2* b, float2* x, cudaStream_t st) {
     const DflGrid G = dfl_grid(ctx);
-    const int wpb = 4;
-    ProfScope prof(ctx, "dfl_coarse", (double)G.Nb * 9 * F.dfl_Ns * (F.dfl_Ns + 1) * 8.0, st);
-    k_dfl_coarse<<<(G.Nb + wpb - 1) / wpb, 32 * wpb, 0, st>>>(G, F.dfl_Ns, F.dfl_nbr, F.dfl_A, x, y);
-    QXD_CUDA(ctx, cudaGetLastError());
-    return QXD_OK;
-}
-
-// GCR on A x = b (block grid, FP32 vectors, sums in FP64), restarted every nkv
-// steps, x from zero, until |b - A x| <= tol |b| or nmx steps
-int coarse_gcr(qxd_ctx* ctx, const QxdFlavour& F, const float2* b, float2* x, int* iters, double* relres,
-               cudaStream_t st) {
-    const DflGrid G = dfl_grid(ctx);
-    const size_t n = (size_t)G.Nb * F.dfl_Ns;  // complex entries
+    const size_t n = (size_t)G.Nb * F.dfl_Ns;
     const int nkv = F.dfl_cnkv;
-    const size_t vb = sizeof(float2) * n;
-    void* slab;
-    QXD_TRY(qxd_ws(ctx, WS_DFL + 1, vb * (2 * nkv + 1), &slab));
-    char* base = static_cast<char*>(slab);
-    auto Pv = [&](int j) { return reinterpret_cast<float2*>(base + vb * j); };
-    auto Wv = [&](int j) { return reinterpret_cast<float2*>(base + vb * (nkv + j)); };
-    float2* r = reinterpret_cast<float2*>(base + vb * 2 * nkv);
-    QXD_CUDA(ctx, cudaMemsetAsync(x, 0, vb, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, st));
-    QXD_TRY(blas_norm2(ctx, 1, n, r, 0, st));
-    QXD_TRY(blas_fetch(ctx, 2, st));
-    const double bb = ctx->red_host[0];
-    *iters = 0;
-    *relres = 0.0;
-    if (!(bb > 0.0)) return QXD_OK;
-    double rr = bb;
-    int it = 0;
-    while (it < F.dfl_cnmx) {
-        for (int k = 0; k < nkv && it < F.dfl_cnmx; ++k) {
-            QXD_CUDA(ctx, cudaMemcpyAsync(Pv(k), r, vb, cudaMemcpyDeviceToDevice, st));
-            QXD_TRY(coarse_apply(ctx, F, Pv(k), Wv(k), st));
-            // orthogonalise w_k (and p_k alike) against the orthonormal w_j, j < k
-            for (int j0 = 0; j0 < k; j0 += kMultiMax) {
-                const int kk = std::min(kMultiMax, k - j0);
-                const void* Wp[kMultiMax];
-                const void* Pp[kMultiMax];
-                for (int i = 0; i < kk; ++i) {
-                    Wp[i] = Wv(j0 + i);
-                    Pp[i] = Pv(j0 + i);
-                }
-                QXD_TRY(blas_multi_dot(ctx, 1, n, kk, Wp, Wv(k), 0, st));
-                QXD_TRY(blas_fetch(ctx, 2 * kk, st));
-                double cre[kMultiMax], cim[kMultiMax];
-                for (int i = 0; i < kk; ++i) {
-                    cre[i] = -ctx->red_host[2 * i];
-                    cim[i] = -ctx->red_host[2 * i + 1];
-                }
-                QXD_TRY(blas_multi_axpy(ctx, 1, 1, n, kk, cre, cim, Wp, Wv(k), st));
-                QXD_TRY(blas_multi_axpy(ctx, 1, 1, n, kk, cre, cim, Pp, Pv(k), st));
-            }
-            // |w_k|^2 and <w_k, r>
-            {
-                const void* Wp[2] = {Wv(k), r};
-                QXD_TRY(blas_multi_dot(ctx, 1, n, 2, Wp, Wv(k), 0, st));
-                QXD_TRY(blas_fetch(ctx, 4, st));
-            }
-            const double ww = ctx->red_host[0];
-            if (!(ww > 0.0) || !std::isfinite(ww)) {
-                *iters = it;
-                *relres = std::sqrt(rr / bb);
-                return QXD_OK;  // breakdown: keep the current iterate (the outer solver is flexible)
-            }
-            // normalise w_k and p_k alike; <w_k, r> = conj(<r, w_k>)
-            const double sc = 1.0 / std::sqrt(ww);
-            const double ar = ctx->red_host[2] * sc, ai = -ctx->red_host[3] * sc;
-            QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, Wv(k), sc, 0.0, Wv(k), st));
-            QXD_TRY(blas_axpby(ctx, 1, 1, n, 0.0, 0.0, Pv(k), sc, 0.0, Pv(k), st));
-            QXD_TRY(blas_axpby(ctx, 1, 1, n, ar, ai, Pv(k), 1.0, 0.0, x, st));
-            {
-                const void* Wp[1] = {Wv(k)};
-                const double cre[1] = {-ar}, cim[1] = {-ai};
-                QXD_TRY(blas_multi_axpy_norm(ctx, 1, n, 1, cre, cim, Wp, r, 0, st));
-                QXD_TRY(blas_fetch(ctx, 2, st));
-            }
-            rr = ctx->red_host[0];
-            ++it;
-            if (rr <= F.dfl_ctol * F.dfl_ctol * bb) {
-                *iters = it;
-                *relres = std::sqrt(rr / bb);
-                return QXD_OK;
-            }
-        }
+    int nsm = 0, per = 0;
+    QXD_CUDA(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    QXD_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_dfl_gcr, kCgThreads, 0));
+    if (per < 1 || nsm < 1) return qxd_fail(ctx, QXD_ECUDA, "little-system solver: kernel does not fit on an SM");
+    // every CTA resident at once (the grid barrier needs it); QXD_DFL_CTAS caps the count
+    // (a test forces several blocks per warp with it)
+    int nblk = std::min(per * nsm, (G.Nb + kCgWarps - 1) / kCgWarps);
+    if (const char* env = std::getenv("QXD_DFL_CTAS")) {
+        const int cap = std::atoi(env);
+        if (cap >= 1) nblk = std::min(nblk, cap);
     }
-    *iters = it;
-    *relres = std::sqrt(rr / bb);
+    nblk = std::max(nblk, 1);
+    const size_t vb = sizeof(float2) * n;
+    const size_t pb = sizeof(double) * 3 * (size_t)nblk * kCgPart;
+    void* slab;
+    QXD_TRY(qxd_ws(ctx, WS_DFL + 1, pb + vb * (2 * nkv + 1) + sizeof(CgBar), &slab));
+    char* base = static_cast<char*>(slab);
+    CgArgs a;
+    a.G = G;
+    a.Ns = F.dfl_Ns;
+    a.nkv = nkv;
+    a.nmx = F.dfl_cnmx;
+    a.tol2 = F.dfl_ctol * F.dfl_ctol;
+    a.cancel = 0.01;
+    if (const char* env = std::getenv("QXD_DFL_CANCEL")) a.cancel = std::atof(env);  // > 1: always explicit
+    a.nbr = F.dfl_nbr;
+    a.A = F.dfl_A;
+    a.b = b;
+    a.x = x;
+    a.part = reinterpret_cast<double*>(base);
+    a.r = reinterpret_cast<float2*>(base + pb);
+    a.P = reinterpret_cast<float2*>(base + pb + vb);
+    a.W = reinterpret_cast<float2*>(base + pb + vb * (1 + nkv));
+    a.bar = reinterpret_cast<CgBar*>(base + pb + vb * (1 + 2 * nkv));
+    a.stat = static_cast<CgStat*>(F.dfl_stat);
+    QXD_CUDA(ctx, cudaMemsetAsync(a.bar, 0, sizeof(CgBar), st));
+    void* args[] = {&a};
+    ProfScope prof(ctx, "dfl_gcr", 0.0, st);
+    QXD_CUDA(ctx, cudaLaunchCooperativeKernel((const void*)k_dfl_gcr, dim3(nblk), dim3(kCgThreads), args, 0, st));
     return QXD_OK;
 }
 
 }  // namespace
+
+// the last little-system solve's step count and residual (synchronises the stream); an
+// error if a grid barrier of any solve since the set-up gave up waiting
+int dfl_status(qxd_ctx* ctx, int fl, int* iters, double* relres, cudaStream_t st) {
+    const QxdFlavour& F = ctx->fl[fl];
+    if (!F.dfl_stat) return QXD_OK;
+    CgStat h{};
+    QXD_CUDA(ctx, cudaMemcpyAsync(&h, F.dfl_stat, sizeof(CgStat), cudaMemcpyDeviceToHost, st));
+    QXD_CUDA(ctx, cudaStreamSynchronize(st));
+    if (h.err) return qxd_fail(ctx, QXD_ECUDA, "little-system solver: a grid barrier gave up waiting");
+    if (iters) *iters = h.iters;
+    if (relres) *relres = h.relres;
+    return QXD_OK;
+}
 
 // out = M_dfl v on full FP32 fields (v, out distinct)
 int dfl_apply_full(qxd_ctx* ctx, int fl, const float4* v, float4* out, int* citers, double* crel, cudaStream_t st) {
@@ -484,11 +787,14 @@ int dfl_apply_full(qxd_ctx* ctx, int fl, const float4* v, float4* out, int* cite
     QXD_TRY(qxd_ws(ctx, WS_DFL + 5, 2 * hb, &t));
     // u = P A^-1 P^+ v
     QXD_TRY(launch_dots(ctx, F.dfl_basis, F.dfl_Ns, v, static_cast<float2*>(c), st));
-    int it = 0;
-    double rel = 0.0;
-    QXD_TRY(coarse_gcr(ctx, F, static_cast<const float2*>(c), static_cast<float2*>(y), &it, &rel, st));
-    if (citers) *citers = it;
-    if (crel) *crel = rel;
+    QXD_TRY(coarse_gcr(ctx, F, static_cast<const float2*>(c), static_cast<float2*>(y), st));
+    if (citers || crel) {
+        int it = 0;
+        double rel = 0.0;
+        QXD_TRY(dfl_status(ctx, fl, &it, &rel, st));
+        if (citers) *citers = it;
+        if (crel) *crel = rel;
+    }
     float4* uf = static_cast<float4*>(u);
     float4* tf = static_cast<float4*>(t);
     QXD_TRY(launch_prolong(ctx, F.dfl_basis, F.dfl_Ns, static_cast<const float2*>(y), 1.f, 0, uf, st));
@@ -520,9 +826,11 @@ void dfl_free(QxdFlavour& F) {
     cudaFree(F.dfl_basis);
     cudaFree(F.dfl_A);
     cudaFree(F.dfl_nbr);
+    cudaFree(F.dfl_stat);
     F.dfl_basis = nullptr;
     F.dfl_A = nullptr;
     F.dfl_nbr = nullptr;
+    F.dfl_stat = nullptr;
     F.dfl_Ns = 0;
 }
 
@@ -550,6 +858,8 @@ int qxd_dfl_setup(qxd_ctx* ctx, int fl, const qxd_dfl_params* prm, const void* s
     QXD_CUDA(ctx, cudaMalloc(&F.dfl_basis, sizeof(float4) * fs * Ns));
     QXD_CUDA(ctx, cudaMalloc(&F.dfl_A, sizeof(float2) * (size_t)G.Nb * 9 * Ns * Ns));
     QXD_CUDA(ctx, cudaMalloc(&F.dfl_nbr, sizeof(int) * (size_t)G.Nb * 9));
+    QXD_CUDA(ctx, cudaMalloc(&F.dfl_stat, sizeof(CgStat)));
+    QXD_CUDA(ctx, cudaMemsetAsync(F.dfl_stat, 0, sizeof(CgStat), st));
     F.dfl_Ns = Ns;
     F.dfl_ctol = prm->ctol;
     F.dfl_cnmx = prm->cnmx;

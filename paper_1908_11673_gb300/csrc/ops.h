@@ -22,6 +22,13 @@ int op_Dw(qxd_ctx* ctx, int fl, int P, const Full& in, const Full& out, cudaStre
 // out_e = Dhat in_e = A_ee in_e - H_eo A_oo^-1 H_oe in_e (dagger: gamma5 Dhat gamma5); tmp_o: odd scratch
 int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out_e, void* tmp_o, cudaStream_t st,
             int nrhs = 1);
+// Dhat on FP32 even fields (no dagger, one right-hand side) with the inner products of
+// a GCR step fused into the second half: result[slot + 2j, +1] = <W_j, out_e> (j < k <= 8),
+// [slot + 2k, +1] = <in_e, out_e>, [slot + 2k + 2] = |out_e|^2 over finite sites,
+// [slot + 2k + 3] = number of sites where it is not finite
+int op_Dhat_dots(qxd_ctx* ctx, int fl, const void* in_e, void* out_e, void* tmp_o, int k, const void* const* W,
+                 int slot, cudaStream_t st);
+int launch_hop_dots(qxd_ctx* ctx, int fl, const HopArgs& a, int k, const void* const* W, int slot, cudaStream_t st);
 // b_e = r_e - H_eo A_oo^-1 r_o  (even-odd preconditioned source)
 int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st, int nrhs = 1);
 // x_o = A_oo^-1 (r_o - H_oe x_e)
@@ -45,6 +52,8 @@ int sap_check(qxd_ctx* ctx);
 // residual reported if the pointers are given); z_e = (M_dfl (r_e, 0))_e on FP32 even fields
 int dfl_apply_full(qxd_ctx* ctx, int fl, const float4* v, float4* out, int* citers, double* crel, cudaStream_t st);
 int dfl_apply_even(qxd_ctx* ctx, int fl, const void* r_e, void* z_e, cudaStream_t st);
+int dfl_status(qxd_ctx* ctx, int fl, int* iters, double* relres, cudaStream_t st);
+void dfl_free(QxdFlavour& F);
 
 // solvers.cu
 int solve_cgne64(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, const Full& x, qxd_info* info,

@@ -30,6 +30,7 @@ struct QxdFlavour {
     float4* dfl_basis = nullptr;  // [Ns] full FP32 fields, block-orthonormal
     float2* dfl_A = nullptr;      // little operator [Nb][9][Ns][Ns]
     int* dfl_nbr = nullptr;       // block neighbours [Nb][9]
+    void* dfl_stat = nullptr;     // status of the little-system solves (steps, residual, barrier error)
     int dfl_Ns = 0, dfl_cnmx = 0, dfl_cnkv = 0;
     double dfl_ctol = 0.0;
 };

@@ -7,6 +7,8 @@ stream) and prints, per solve, the solver report and the kernel table.
 
     python -m paper_1908_11673_gb300.solve_profile --L 24,24,24,48 --precond sap [--ncy 5 --nmr 5]
     python -m paper_1908_11673_gb300.solve_profile --L 24,24,24,48 --precond dfl --Ns 12 --ninv 2
+    python -m paper_1908_11673_gb300.solve_profile --L 64,32,32,32 --cstar 3 --qhat 4 --kappa 0.137312 \
+        --seed 2100 --sigma-h 0.6 --precond dfl --ncy 3 --nmr 4      # rough fields, C* boundary
 
 With --precond dfl the deflation subspace is built first (qxd_dfl_setup) from
 Ns Gaussian fields drawn on the device with a seeded torch generator; its
@@ -31,6 +33,8 @@ def main(argv=None):
     ap.add_argument("--kappa", type=float, default=0.136377)
     ap.add_argument("--seed", type=int, default=2000)
     ap.add_argument("--stout", type=int, default=5)
+    ap.add_argument("--sigma-h", type=float, default=0.3,
+                    help="width of the random Hermitian generators (0.6: rough fields, plaquette about 0.63)")
     ap.add_argument("--solver", choices=["fgcr", "cgne"], default="fgcr")
     ap.add_argument("--precond", choices=["none", "sap", "dfl"], default="none")
     ap.add_argument("--Ns", type=int, default=12)
@@ -48,7 +52,7 @@ def main(argv=None):
 
     build.build()
     L = tuple(int(v) for v in args.L.split(","))
-    U, A = workload.gauge_field(L, args.seed, stout_steps=args.stout)
+    U, A = workload.gauge_field(L, args.seed, sigma_h=args.sigma_h, stout_steps=args.stout)
     ctx = qxd.Context(L, args.cstar, (np.pi, 0.0, 0.0, 0.0))
     ctx.set_links(U, A, 6.0)
     ctx.set_clover(0, args.qhat, args.kappa, 1.90952, 1.0)

@@ -107,3 +107,31 @@ def test_dfl_errors():
         ctx.dfl_setup(0, seeds(V, 33, 3), 33)
     assert e.value.code == 1
     ctx.close()
+
+
+@pytest.mark.parametrize("Ns,cnkv,ctas,cancel", [(12, 6, None, None), (12, 6, "1", None), (7, 5, "1", "2"),
+                                                 (20, 4, None, "2")])
+def test_dfl_little_solver(monkeypatch, Ns, cnkv, ctas, cancel):
+    """The little-system GCR (one cooperative launch, grid barriers, sums reduced on every
+    CTA): M_dfl v against the oracle's exact little solve on the GPU's own basis, on 32
+    blocks, with restarts (cnkv below the step count), several blocks per warp
+    (QXD_DFL_CTAS=1: one CTA of 16 warps), Ns that leaves lanes idle (7: four rows of A side
+    by side in 28 lanes), and the explicit-norm step forced (QXD_DFL_CANCEL=2)."""
+    if ctas:
+        monkeypatch.setenv("QXD_DFL_CTAS", ctas)
+    if cancel:
+        monkeypatch.setenv("QXD_DFL_CANCEL", cancel)
+    qxd, ctx, op, _, _ = setup((16, 8, 8, 8), 0, (np.pi, 0, 0, 0), qhat=-2, kappa=0.13, seed=9430, stout=1)
+    V = op.geom.V
+    ctx.set_sap(2, 3)
+    ctx.dfl_setup(0, seeds(V, Ns, 9431), Ns, ninv=1, ctol=1e-7, cnmx=5000, cnkv=cnkv)
+    sap = SAP(op, bsize=4, ncy=2, nmr=3)
+    mine = Deflation.from_basis(op, sap, gpu_basis(ctx, V, Ns).astype(np.complex128))
+    assert mine.nblocks == 32
+    v = workload.spinor(V, 9432).astype(np.complex64)
+    out = np.empty_like(v)
+    info = ctx.dfl_apply(0, v, out)
+    assert info.true_relres <= 1e-7
+    assert info.iters > cnkv  # restarted at least once
+    assert relerr(out.astype(np.complex128), mine.apply(v.astype(np.complex128))) <= 1e-4
+    ctx.close()
