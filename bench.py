@@ -57,6 +57,9 @@ FP64_PEAK_TFLOPS = 1.19
 # on the 24^3x48 lattice for the current kernels;
 # a launch on another lattice moves these bytes times its V/2 sites.
 NCU_BYTES_PER_SITE = {"hop_fp32_self1_post0": 1000.6, "hop_fp32_self0_post1": 898.4}
+# DRAM bytes over algorithmic bytes, measured the same way, for kernels whose bytes per
+# launch vary (the hop with fused inner products reads one field per earlier basis field)
+NCU_TRAFFIC_RATIO = {"hop_fp32_self1_post0_dots": 1.021}
 
 
 GOLDEN_RATIONAL = os.path.join(ROOT, "tests", "golden", "rational_deg10_pow_m1_4.txt")
@@ -673,12 +676,18 @@ def run_native(args, w, name):
     else:
         achieved = bytes_per_launch / (mean_ms * 1e-3) / 1e9
         per_site = NCU_BYTES_PER_SITE.get(dom["name"])
+        ratio = NCU_TRAFFIC_RATIO.get(dom["name"])
+        if per_site:
+            traffic, source = per_site * (V // 2), "ncu dram bytes per site on 24^3x48 scaled to this lattice"
+        elif ratio:
+            traffic = ratio * bytes_per_launch
+            source = "ncu dram bytes / algorithmic bytes on 24^3x48 times this launch's mean algorithmic bytes"
+        else:
+            traffic, source = None, None
         roofline = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (HBM copy bandwidth)",
                     "bytes_per_launch": bytes_per_launch, "mean_launch_ms": mean_ms,
-                    "traffic": per_site * (V // 2) if per_site else None,
-                    "traffic_source": "ncu dram bytes per site on 24^3x48 scaled to this lattice" if per_site else None,
-                    "timing": timing}
+                    "traffic": traffic, "traffic_source": source, "timing": timing}
     kernels = []
     for p in sorted(prof, key=lambda p: -p["ms"]):
         gbs = p["bytes"] / (p["ms"] * 1e-3) / 1e9 if p["ms"] > 0 else None

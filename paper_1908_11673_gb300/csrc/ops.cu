@@ -59,6 +59,27 @@ int op_Dhat(qxd_ctx* ctx, int fl, int P, int dagger, const void* in_e, void* out
     return launch_hop(ctx, fl, P, a, st);
 }
 
+int op_Dhat_dots(qxd_ctx* ctx, int fl, const void* in_e, void* out_e, void* tmp_o, int k, const void* const* W,
+                 int slot, cudaStream_t st) {
+    HopArgs a{};
+    a.nrhs = 1;
+    a.pout = 1;
+    a.in_nb = in_e;
+    a.out = tmp_o;
+    a.self_mode = 0;
+    a.post_mode = 1;
+    a.c_hop = 1.0;
+    QXD_TRY(launch_hop(ctx, fl, QXD_FP32, a, st));
+    a.pout = 0;
+    a.in_nb = tmp_o;
+    a.in_self = in_e;
+    a.out = out_e;
+    a.self_mode = 1;
+    a.post_mode = 0;
+    a.c_hop = -1.0;
+    return launch_hop_dots(ctx, fl, a, k, W, slot, st);
+}
+
 int op_eo_source(qxd_ctx* ctx, int fl, int P, const Full& r, void* b_e, void* tmp_o, cudaStream_t st, int nrhs) {
     QXD_TRY(launch_diag(ctx, fl, P, 1, 1, r.o, tmp_o, nrhs, st));
     HopArgs a{};

@@ -250,17 +250,26 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
         for (int k = 0; k < nkv; ++k) {
             if (!rz) QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, r, Z[k], ztmp, st));
             const void* rk = rz ? Z[k] : r;  // current residual
-            QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Z[k], W[k], to, st));
             // <W_j, w_k> for j < k and <r, w_k>; without a preconditioner also |w_k|^2,
             // from which |w_k'|^2 of the orthogonalised w_k' follows (the W_j are
-            // orthogonal), so that orthogonalisation and residual update run as one pass
-            for (int j = 0; j < k; ++j) Wc[j] = W[j];
-            int nd = k;
-            if (!split) Wc[nd++] = rk;
-            if (rz) Wc[nd++] = W[k];
-            if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), W[k], 0, st));
-            if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, r, W[k], 2 * k, st));
-            QXD_TRY(blas_fetch(ctx, 2 * nd + (split ? 2 : 0), st));
+            // orthogonal), so that orthogonalisation and residual update run as one pass.
+            // In FP32 with up to 8 earlier fields the products come from the operator's
+            // own second launch (op_Dhat_dots), which also counts non-finite sites.
+            double nonfinite = 0.0;
+            if (rz && Pb == QXD_FP32 && k <= kMultiMax) {
+                QXD_TRY(op_Dhat_dots(ctx, fl, Z[k], W[k], to, k, W.data(), 0, st));
+                QXD_TRY(blas_fetch(ctx, 2 * k + 4, st));
+                nonfinite = ctx->red_host[2 * k + 3];
+            } else {
+                QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Z[k], W[k], to, st));
+                for (int j = 0; j < k; ++j) Wc[j] = W[j];
+                int nd = k;
+                if (!split) Wc[nd++] = rk;
+                if (rz) Wc[nd++] = W[k];
+                if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), W[k], 0, st));
+                if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, r, W[k], 2 * k, st));
+                QXD_TRY(blas_fetch(ctx, 2 * nd + (split ? 2 : 0), st));
+            }
             for (int j = 0; j < k; ++j) {
                 Rre[j * nkv + k] = ctx->red_host[2 * j] / ww[j];
                 Rim[j * nkv + k] = ctx->red_host[2 * j + 1] / ww[j];
@@ -282,7 +291,7 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
                 if (std::isfinite(w2o) && w2o > 0.01 * w2) {
                     fused = true;
                     ww[k] = w2o;
-                    ctx->red_host[1] = 0.0;  // non-finite count: the dot pass found none
+                    ctx->red_host[1] = nonfinite;  // non-finite count (the separate dot pass counts none)
                 }
             }
             if (!fused) {
