@@ -345,8 +345,14 @@ int fgcr_inner(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const void* b, 
                 QXD_TRY(op_Dhat(ctx, fl, Pb, 0, e, tmp, to, st));
             }
             QXD_CUDA(ctx, cudaMemcpyAsync(r, b, hv, cudaMemcpyDeviceToDevice, st));
-            QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -1.0, 0.0, tmp, 1.0, 0.0, r, st));
-            QXD_TRY(blas_norm2(ctx, Pv, n, r, 0, st));
+            if (!split) {  // r -= tmp and |r|^2 in one pass
+                const void* Xp[1] = {tmp};
+                const double cr[1] = {-1.0}, ci[1] = {0.0};
+                QXD_TRY(blas_multi_axpy_norm(ctx, Pv, n, 1, cr, ci, Xp, r, 0, st));
+            } else {
+                QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -1.0, 0.0, tmp, 1.0, 0.0, r, st));
+                QXD_TRY(blas_norm2(ctx, Pv, n, r, 0, st));
+            }
             QXD_TRY(blas_fetch(ctx, 2, st));
             rr = ctx->red_host[0];
             if (rr <= rtol * rtol * bn * bn) done = true;
