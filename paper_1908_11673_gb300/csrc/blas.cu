@@ -258,22 +258,79 @@ int blas_dot(qxd_ctx* ctx, int pa, int pb, size_t n, const void* a, const void* 
 
 // ---- double-float conversions (FP64 layout <-> double-float layout, same 16-byte chunks) ----
 // elementwise; in and out may be the same array
+// The conversions go through the integer forms of df64.cuh (df_split, df_widen): the
+// FP64 <-> FP32 conversion instructions would load the FP64 pipe.  Each thread keeps
+// kUnroll independent 16-byte loads in flight (in == out allowed: every entry is read
+// and written by the same thread).
 __global__ void k_split_df64(const double2* in, float4* out, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const double2 d = in[i];
-        const dfl a(d.x), b(d.y);
-        out[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += S * kUnroll) {
+        double2 d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n) d[u] = in[i0 + u * S];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n) {
+                const dfl a = df_split(d[u].x), b = df_split(d[u].y);
+                out[i0 + u * S] = make_float4(a.hi, a.lo, b.hi, b.lo);
+            }
     }
 }
+// the same, with result[0] = |in|^2 over the finite entries and result[1] = count of the
+// others; an entry's |d|^2 is hi (hi + 2 lo) per component in FP32 (about 2^-23 relative)
+// where that lies in [1e-30, 1e30], else FP64 (zero entries add nothing)
+__global__ void __launch_bounds__(kRedThreads) k_split_df64_norm(const double2* in, float4* out, size_t n, RedOut o) {
+    double v[2] = {0.0, 0.0};
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += S * kUnroll) {
+        double2 d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n) d[u] = in[i0 + u * S];
+        float fs = 0.f;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n) {
+                const dfl a = df_split(d[u].x), b = df_split(d[u].y);
+                out[i0 + u * S] = make_float4(a.hi, a.lo, b.hi, b.lo);
+                const float f = fmaf(a.hi, fmaf(2.f, a.lo, a.hi), b.hi * fmaf(2.f, b.lo, b.hi));
+                if (f >= 1e-30f && f <= 1e30f) {
+                    fs += f;
+                } else if (((df_bits(d[u].x) | df_bits(d[u].y)) << 1) != 0) {
+                    const double dd = d[u].x * d[u].x + d[u].y * d[u].y;
+                    if (isfinite(dd)) v[0] += dd;
+                    else v[1] += 1.0;
+                }
+            }
+        v[0] += fs;
+    }
+    block_reduce_finish<2>(v, o);
+}
 __global__ void k_join_df64(const float4* in, double2* out, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float4 v = in[i];
-        out[i] = make_double2(to_double(dfl(v.x, v.y)), to_double(dfl(v.z, v.w)));
+    const size_t S = (size_t)gridDim.x * blockDim.x;
+    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += S * kUnroll) {
+        float4 f[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n) f[u] = in[i0 + u * S];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i0 + u * S < n)
+                out[i0 + u * S] = make_double2(df_widen(f[u].x) + df_widen(f[u].y), df_widen(f[u].z) + df_widen(f[u].w));
     }
 }
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st) {
     ProfScope prof(ctx, "split_df64", (double)n * 32, st);
     k_split_df64<<<upd_blocks(ctx, n), 256, 0, st>>>(static_cast<const double2*>(in), static_cast<float4*>(out), n);
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+int blas_split_df64_norm(qxd_ctx* ctx, const void* in, void* out, size_t n, int slot, cudaStream_t st) {
+    ProfScope prof(ctx, "split_df64", (double)n * 32, st);
+    const RedOut o = red_out(ctx, slot);
+    k_split_df64_norm<<<wave_blocks(ctx, k_split_df64_norm, kRedThreads, (size_t)kRedThreads * 4, n), kRedThreads, 0,
+                        st>>>(static_cast<const double2*>(in), static_cast<float4*>(out), n, o);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }

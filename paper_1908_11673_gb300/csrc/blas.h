@@ -32,6 +32,9 @@ int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStrea
 // Double-float conversions over n complex numbers (16-byte chunks): FP64 -> double-float
 // and double-float -> FP64 (in == out allowed for both)
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
+// the same split (in != out), with result[slot] = |in|^2 over finite entries (about 2^-23
+// relative) and result[slot+1] = number of non-finite entries
+int blas_split_df64_norm(qxd_ctx* ctx, const void* in, void* out, size_t n, int slot, cudaStream_t st);
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
 // The mixed solver's outer loop on double-float half-lattice fields (FP32 pipe only):
 // r32 = FP32(eta - dx) with result[slot] = |r|^2, result[slot+1] = non-finite sites;

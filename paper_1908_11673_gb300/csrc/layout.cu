@@ -1,6 +1,9 @@
 // Conversions between the canonical spinor layout of the C ABI
 // ([site][4][3] complex, lexicographic over the simulated lattice, or over the
 // sites of one parity) and the internal parity-split structure-of-arrays fields.
+#include <type_traits>
+
+#include "df64.cuh"
 #include "qxd_internal.h"
 
 namespace qxd {
@@ -39,30 +42,56 @@ __global__ void k_pack(Geo g, const void* __restrict__ canon, int cfull, int p, 
     store_spinor<PINT>(static_cast<CH*>(internal) + (size_t)rhs * Prec<PINT>::nchunk * g.Vh, g.Vh, h, s);
 }
 
+// The canonical layout keeps a site's 12 complex numbers together, and the sites of one
+// parity are every other site: a thread writing its own site would write 16-byte pieces
+// 384 bytes apart across the warp (half sectors).  So each warp stages its 32 sites in
+// shared memory and then writes them as consecutive pieces, lane by lane.
 template <int PINT, int COUT>
-__global__ void k_unpack(Geo g, const void* __restrict__ internal, int p, void* __restrict__ canon, int cfull) {
+__global__ void __launch_bounds__(kThreads) k_unpack(Geo g, const void* __restrict__ internal, int p,
+                                                     void* __restrict__ canon, int cfull) {
     using R = typename Prec<PINT>::real;
     using CH = typename Prec<PINT>::chunk;
+    using OT = typename std::conditional<COUT == 0, double2, float2>::type;
+    constexpr int kPad = 13;  // staging row of one site (12 values and one pad against bank conflicts)
+    __shared__ OT stage[kThreads / 32][32 * kPad];
+    __shared__ long long dst[kThreads / 32][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= g.Vh) return;
     const int rhs = blockIdx.y;
-    long long site = h;
-    if (cfull) {
-        int x[4];
-        site_coords(g, p, h, x);
-        site = lex_index(g, x);
-    }
     const long long nsites = cfull ? g.V : g.Vh;
-    cplx<R> s[12];
-    load_spinor<PINT>(static_cast<const CH*>(internal) + (size_t)rhs * Prec<PINT>::nchunk * g.Vh, g.Vh, h, s);
-    if (COUT == 0) {
-        double2* c = static_cast<double2*>(canon) + ((long long)rhs * nsites + site) * 12;
+    if (h < g.Vh) {
+        long long site = h;
+        if (cfull) {
+            int x[4];
+            site_coords(g, p, h, x);
+            site = lex_index(g, x);
+        }
+        cplx<R> s[12];
+        load_spinor<PINT>(static_cast<const CH*>(internal) + (size_t)rhs * Prec<PINT>::nchunk * g.Vh, g.Vh, h, s);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) c[k] = make_double2((double)s[k].re, (double)s[k].im);
+        for (int k = 0; k < 12; ++k) {
+            OT v;
+            if constexpr (COUT == 0 && PINT != 0) {  // FP32 to FP64 by integer operations
+                v.x = df_widen(s[k].re);
+                v.y = df_widen(s[k].im);
+            } else {
+                v.x = s[k].re;
+                v.y = s[k].im;
+            }
+            stage[warp][lane * kPad + k] = v;
+        }
+        dst[warp][lane] = ((long long)rhs * nsites + site) * 12;
     } else {
-        float2* c = static_cast<float2*>(canon) + ((long long)rhs * nsites + site) * 12;
+        dst[warp][lane] = -1;
+    }
+    __syncwarp();
+    OT* c = static_cast<OT*>(canon);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) c[k] = make_float2((float)s[k].re, (float)s[k].im);
+    for (int j0 = 0; j0 < 12; ++j0) {
+        const int j = j0 * 32 + lane;  // value j of the warp: site j / 12, component j % 12
+        const int sl = j / 12, k = j - sl * 12;
+        const long long d = dst[warp][sl];
+        if (d >= 0) c[d + k] = stage[warp][sl * kPad + k];
     }
 }
 

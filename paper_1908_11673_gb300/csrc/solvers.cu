@@ -401,8 +401,13 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 34, hb64, &dxe));
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 35, hb64, &dxo));
     }
-    QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
-    QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
+    if (df) {  // the source's double-float copy and its norm in one pass per half
+        QXD_TRY(blas_split_df64_norm(ctx, eta.e, ede, n, 0, st));
+        QXD_TRY(blas_split_df64_norm(ctx, eta.o, edo, n, 2, st));
+    } else {
+        QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
+        QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
+    }
     QXD_TRY(blas_fetch(ctx, 4, st));
     QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "source"));
     const double enorm = std::sqrt(ctx->red_host[0] + ctx->red_host[2]);
@@ -417,8 +422,6 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         return QXD_OK;
     }
     if (df) {
-        QXD_TRY(blas_split_df64(ctx, eta.e, ede, n, st));
-        QXD_TRY(blas_split_df64(ctx, eta.o, edo, n, st));
         QXD_CUDA(ctx, cudaMemsetAsync(xde, 0, hb64, st));
         QXD_CUDA(ctx, cudaMemsetAsync(xdo, 0, hb64, st));
         QXD_TRY(blas_df_to_f32(ctx, ede, tP, st));

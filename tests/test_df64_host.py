@@ -92,3 +92,69 @@ def test_lazy_chain_accuracy(prog):
         scale = sum(abs(Fraction(float(u)) * Fraction(float(v))) for u, v in zip(x, y))
         err = abs(Fraction(hi) + Fraction(lo) - exact)
         assert err <= scale * Fraction(1, 2 ** 44), float(err / scale)
+
+
+CONVERSIONS = r'''
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include "df64.cuh"
+using namespace qxd;
+// df_split and df_widen (integer forms) against the conversion operators they replace:
+// (float)d, (float)(d - (double)(float)d) and (double)f, compared bit for bit
+int main() {
+    std::mt19937_64 rng(7);
+    long long bad = 0, n = 0;
+    auto check = [&](double d) {
+        const dfl a = df_split(d);
+        const float rh = (float)d, rl = (float)(d - (double)rh);
+        const double w = df_widen(rh), rw = (double)rh;
+        ++n;
+        if (std::memcmp(&a.hi, &rh, 4) || std::memcmp(&a.lo, &rl, 4) || std::memcmp(&w, &rw, 8)) {
+            if (bad < 5) std::printf("mismatch %a\n", d);
+            ++bad;
+        }
+    };
+    std::uniform_real_distribution<double> U(-4.0, 4.0);
+    for (int i = 0; i < 1000000; ++i) {
+        unsigned long long u = rng();
+        double d;
+        std::memcpy(&d, &u, 8);
+        check(d);  // any bit pattern: subnormal, inf, nan, huge and tiny values included
+        check(U(rng) * std::ldexp(1.0, (int)(rng() % 80) - 40));
+        u = (rng() & ~0x1FFFFFFFull) | 0x10000000ull;  // ties of the leading part
+        std::memcpy(&d, &u, 8);
+        check(d);
+        u = (rng() & 0xFFF0000000000000ull) | 0xFFFFFF0000000ull | (rng() & 0x1FFFFFFFull);  // carries
+        std::memcpy(&d, &u, 8);
+        check(d);
+    }
+    const double edge[] = {0.0, -0.0, 1.0, -1.0, 0x1p-74, 0x1p-75, 0x1.fffffffffffffp-75, 0x1p127,
+                           0x1.fffffep127, 0x1.ffffffp127, 0x1.fffffffffffffp126, 1e300, -1e-300, 5e-324,
+                           INFINITY, -INFINITY, NAN, 0x1.000001p0, 0x1.0000008p0, 0x1.0000018p0, 0x1.ffffff8p0};
+    for (double d : edge) check(d);
+    std::printf("%lld %lld\n", n, bad);
+    return 0;
+}
+'''
+
+
+def test_integer_conversions_match_the_conversion_operators(tmp_path):
+    """df_split / df_widen (integer forms used by the solver's conversion kernels) give the
+    same bits as the IEEE conversions (round to nearest even) on 4 M random doubles:
+    arbitrary bit patterns, values of spinor magnitude, exact ties and rounding carries
+    of the leading part, and edge cases (signed zeros, range limits, inf, nan)."""
+    cxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cxx or not os.path.isdir(cuda_inc):
+        pytest.skip("needs g++ and the CUDA headers")
+    src = tmp_path / "conv.cpp"
+    src.write_text(CONVERSIONS)
+    exe = tmp_path / "conv"
+    subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-I", cuda_inc,
+                    "-I", os.path.join(ROOT, "paper_1908_11673_gb300", "csrc"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    n, bad = int(out[-2]), int(out[-1])
+    assert n > 4_000_000 and bad == 0, out
