@@ -62,3 +62,31 @@ def test_noalloc_rejects_host_arrays_and_large_lattices():
         big.apply_Dhat_eo_noalloc(0, 0, x, torch.empty_like(x))
     assert e.value.code == 1 and "at most 32768" in str(e.value)
     big.close()
+
+
+def test_noalloc_call_records_into_a_cuda_graph():
+    """No allocation and no host wait inside the call: after a first call (which looks up
+    the scratch array's address) it records into a CUDA graph, and the replay gives
+    qxd_apply_Dhat_eo's result for the input present at replay time."""
+    import torch
+    qxd, ctx, op, _, _ = setup((6, 4, 6, 4), 2, (np.pi, 0.0, 0.0, 0.0), qhat=-2, seed=5100)
+    ne = op.geom.V // 2
+    psi = torch.from_numpy(workload.spinor(ne, 5300)).to(torch.complex64).cuda()
+    got = torch.empty_like(psi)
+    ref = torch.empty_like(psi)
+    ctx.apply_Dhat_eo_noalloc(0, 1, psi, got)
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ctx.apply_Dhat_eo_noalloc(0, 1, psi, got, stream=s)
+    psi.copy_(torch.from_numpy(workload.spinor(ne, 5301)).to(torch.complex64))
+    got.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    ctx.apply_Dhat_eo(0, 1, psi, ref)
+    torch.cuda.synchronize()
+    r = ref.cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(r) > 0
+    assert relerr(got.cpu().numpy().astype(np.complex128), r) <= TOL[1]
+    ctx.close()
