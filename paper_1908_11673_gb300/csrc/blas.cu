@@ -277,36 +277,6 @@ __global__ void k_split_df64(const double2* in, float4* out, size_t n) {
             }
     }
 }
-// the same, with result[0] = |in|^2 over the finite entries and result[1] = count of the
-// others; an entry's |d|^2 is hi (hi + 2 lo) per component in FP32 (about 2^-23 relative)
-// where that lies in [1e-30, 1e30], else FP64 (zero entries add nothing)
-__global__ void __launch_bounds__(kRedThreads) k_split_df64_norm(const double2* in, float4* out, size_t n, RedOut o) {
-    double v[2] = {0.0, 0.0};
-    const size_t S = (size_t)gridDim.x * blockDim.x;
-    for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += S * kUnroll) {
-        double2 d[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (i0 + u * S < n) d[u] = in[i0 + u * S];
-        float fs = 0.f;
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (i0 + u * S < n) {
-                const dfl a = df_split(d[u].x), b = df_split(d[u].y);
-                out[i0 + u * S] = make_float4(a.hi, a.lo, b.hi, b.lo);
-                const float f = fmaf(a.hi, fmaf(2.f, a.lo, a.hi), b.hi * fmaf(2.f, b.lo, b.hi));
-                if (f >= 1e-30f && f <= 1e30f) {
-                    fs += f;
-                } else if (((df_bits(d[u].x) | df_bits(d[u].y)) << 1) != 0) {
-                    const double dd = d[u].x * d[u].x + d[u].y * d[u].y;
-                    if (isfinite(dd)) v[0] += dd;
-                    else v[1] += 1.0;
-                }
-            }
-        v[0] += fs;
-    }
-    block_reduce_finish<2>(v, o);
-}
 __global__ void k_join_df64(const float4* in, double2* out, size_t n) {
     const size_t S = (size_t)gridDim.x * blockDim.x;
     for (size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i0 < n; i0 += S * kUnroll) {
@@ -326,14 +296,6 @@ int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStrea
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }
-int blas_split_df64_norm(qxd_ctx* ctx, const void* in, void* out, size_t n, int slot, cudaStream_t st) {
-    ProfScope prof(ctx, "split_df64", (double)n * 32, st);
-    const RedOut o = red_out(ctx, slot);
-    k_split_df64_norm<<<wave_blocks(ctx, k_split_df64_norm, kRedThreads, (size_t)kRedThreads * 4, n), kRedThreads, 0,
-                        st>>>(static_cast<const double2*>(in), static_cast<float4*>(out), n, o);
-    QXD_CUDA(ctx, cudaGetLastError());
-    return QXD_OK;
-}
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st) {
     ProfScope prof(ctx, "join_df64", (double)n * 32, st);
     k_join_df64<<<upd_blocks(ctx, n), 256, 0, st>>>(static_cast<const float4*>(in), static_cast<double2*>(out), n);
@@ -342,16 +304,21 @@ int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream
 }
 
 // ---- the mixed solver's outer loop in double-float (site by site, FP32 pipe only) ----
-// r = eta - dx (both double-float, one half-lattice field): r32 = r rounded to the
-// FP32 layout, result[slot] = |r|^2 (leading parts, FP32 per site, FP64 sums),
-// result[slot+1] = count of non-finite sites
-__global__ void __launch_bounds__(kRedThreads) k_df_residual(int Vh, const float4* __restrict__ eta,
+// r = eta - dx (eta an FP64 half-lattice field, split into double-float on the fly by
+// integer operations; dx double-float): r32 = r rounded to the FP32 layout,
+// result[slot] = |r|^2 (leading parts, FP32 per site, FP64 sums), result[slot+1] =
+// count of non-finite sites
+__global__ void __launch_bounds__(kRedThreads) k_df_residual(int Vh, const double2* __restrict__ eta,
                                                              const float4* __restrict__ dx,
                                                              float4* __restrict__ r32, RedOut o) {
     double v[2] = {0.0, 0.0};
     for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
         cplx<dfl> e[12], d[12];
-        load_spinor<3>(eta, Vh, h, e);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 x = QXD_LDG(eta + (size_t)k * Vh + h);
+            e[k] = {df_split(x.x), df_split(x.y)};
+        }
         load_spinor<3>(dx, Vh, h, d);
         cplx<float> r[12];
         float f = 0.f;
@@ -424,6 +391,39 @@ __global__ void k_df_add_f32(int Vh, const float4* __restrict__ e32, float4* __r
     store_spinor<3>(x, Vh, h, xs);
 }
 
+// r32 = FP32 rounding of an FP64 half-lattice field (integer conversion), result[slot] =
+// its |.|^2 over the finite sites and result[slot+1] = count of the others; a site's
+// |x|^2 is sum hi (hi + 2 lo) in FP32 (about 2^-23 relative) where that lies in
+// [1e-30, 1e30], else FP64
+__global__ void __launch_bounds__(kRedThreads) k_f64_to_f32_norm(int Vh, const double2* __restrict__ x,
+                                                                 float4* __restrict__ r32, RedOut o) {
+    double v[2] = {0.0, 0.0};
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < Vh; h += gridDim.x * blockDim.x) {
+        double2 xs[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) xs[k] = QXD_LDG(x + (size_t)k * Vh + h);
+        cplx<float> r[12];
+        float f = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const dfl a = df_split(xs[k].x), b = df_split(xs[k].y);
+            r[k] = {a.hi, b.hi};
+            f = fmaf(a.hi, fmaf(2.f, a.lo, a.hi), fmaf(b.hi, fmaf(2.f, b.lo, b.hi), f));
+        }
+        if (f >= 1e-30f && f <= 1e30f) {
+            v[0] += f;
+        } else {
+            double dd = 0.0;
+#pragma unroll
+            for (int k = 0; k < 12; ++k) dd += xs[k].x * xs[k].x + xs[k].y * xs[k].y;
+            if (isfinite(dd)) v[0] += dd;
+            else v[1] += 1.0;
+        }
+        store_spinor<1>(r32, Vh, h, r);
+    }
+    block_reduce_finish<2>(v, o);
+}
+
 // r32 = leading parts of a double-float field, one half-lattice field
 __global__ void k_df_to_f32(int Vh, const float4* __restrict__ x, float4* __restrict__ r32) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -441,7 +441,7 @@ int blas_df_residual(qxd_ctx* ctx, const void* eta, const void* dx, void* r32, i
     ProfScope prof(ctx, "df_residual", (double)Vh * (192 + 192 + 96), st);
     const RedOut o = red_out(ctx, slot);
     k_df_residual<<<wave_blocks(ctx, k_df_residual, kRedThreads, (size_t)kRedThreads, (size_t)Vh), kRedThreads, 0,
-                    st>>>(Vh, static_cast<const float4*>(eta), static_cast<const float4*>(dx),
+                    st>>>(Vh, static_cast<const double2*>(eta), static_cast<const float4*>(dx),
                           static_cast<float4*>(r32), o);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
@@ -450,6 +450,15 @@ int blas_df_add_f32(qxd_ctx* ctx, const void* e32, void* x, cudaStream_t st) {
     const int Vh = ctx->g.Vh;
     ProfScope prof(ctx, "df_add_f32", (double)Vh * (96 + 192 + 192), st);
     k_df_add_f32<<<nblocks(Vh, 128), 128, 0, st>>>(Vh, static_cast<const float4*>(e32), static_cast<float4*>(x));
+    QXD_CUDA(ctx, cudaGetLastError());
+    return QXD_OK;
+}
+int blas_f64_to_f32_norm(qxd_ctx* ctx, const void* x, void* r32, int slot, cudaStream_t st) {
+    const int Vh = ctx->g.Vh;
+    ProfScope prof(ctx, "f64_to_f32_norm", (double)Vh * (192 + 96), st);
+    const RedOut o = red_out(ctx, slot);
+    k_f64_to_f32_norm<<<wave_blocks(ctx, k_f64_to_f32_norm, kRedThreads, (size_t)kRedThreads, (size_t)Vh),
+                        kRedThreads, 0, st>>>(Vh, static_cast<const double2*>(x), static_cast<float4*>(r32), o);
     QXD_CUDA(ctx, cudaGetLastError());
     return QXD_OK;
 }

@@ -32,14 +32,14 @@ int blas_norm2(qxd_ctx* ctx, int p, size_t n, const void* a, int slot, cudaStrea
 // Double-float conversions over n complex numbers (16-byte chunks): FP64 -> double-float
 // and double-float -> FP64 (in == out allowed for both)
 int blas_split_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
-// the same split (in != out), with result[slot] = |in|^2 over finite entries (about 2^-23
-// relative) and result[slot+1] = number of non-finite entries
-int blas_split_df64_norm(qxd_ctx* ctx, const void* in, void* out, size_t n, int slot, cudaStream_t st);
+
 int blas_join_df64(qxd_ctx* ctx, const void* in, void* out, size_t n, cudaStream_t st);
-// The mixed solver's outer loop on double-float half-lattice fields (FP32 pipe only):
-// r32 = FP32(eta - dx) with result[slot] = |r|^2, result[slot+1] = non-finite sites;
-// x += e32; r32 = FP32(x)
+// The mixed solver's outer loop on half-lattice fields (FP32 pipe only): with eta FP64
+// and dx double-float, r32 = FP32(eta - dx) with result[slot] = |r|^2, result[slot+1] =
+// non-finite sites; x += e32; r32 = FP32(x) for a double-float x; r32 = FP32(x) for an
+// FP64 x with result[slot] = |x|^2 (about 2^-23 relative), result[slot+1] = non-finite sites
 int blas_df_residual(qxd_ctx* ctx, const void* eta, const void* dx, void* r32, int slot, cudaStream_t st);
+int blas_f64_to_f32_norm(qxd_ctx* ctx, const void* x, void* r32, int slot, cudaStream_t st);
 int blas_df_add_f32(qxd_ctx* ctx, const void* e32, void* x, cudaStream_t st);
 int blas_df_to_f32(qxd_ctx* ctx, const void* x, void* r32, cudaStream_t st);
 // r32 = FP32(b - y - sigma x), b, y, x double-float; result[slot] = |r|^2, [slot+1] = non-finite sites

@@ -375,13 +375,21 @@ int launch_set_flavour(qxd_ctx* ctx, int fl, cudaStream_t st) {
 int ensure_df64(qxd_ctx* ctx, int fl, cudaStream_t st, bool inverse) {
     QxdFlavour& F = ctx->fl[fl];
     const size_t n = 2ull * 36 * ctx->g.Vh;
+    float4** made[3] = {nullptr, nullptr, nullptr};  // copies allocated by this call
+    int nmade = 0;
     auto build = [&](float4** dst, const double2* src) -> int {
         if (*dst) return QXD_OK;
         if (cudaMalloc(dst, n * sizeof(float4)) != cudaSuccess) {
             cudaGetLastError();
             *dst = nullptr;
+            // leave no partial set behind: a caller may go on without the copies
+            for (int i = 0; i < nmade; ++i) {
+                cudaFree(*made[i]);
+                *made[i] = nullptr;
+            }
             return qxd_fail(ctx, QXD_ENOMEM, "double-float copy of the links or site-diagonal terms: allocation failed");
         }
+        made[nmade++] = dst;
         return blas_split_df64(ctx, src, *dst, n, st);
     };
     QXD_TRY(build(&F.Vdf, F.V64));

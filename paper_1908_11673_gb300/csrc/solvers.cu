@@ -373,12 +373,14 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     const size_t n = 12ull * ctx->g.Vh;
     const int P = s->inner;
     const int Pv = vec_prec(P);  // precision of the inner solve's vectors (FP32 for BF16 storage)
-    // Mixed inner precision: the outer loop holds eta, x and D x as double-float
-    // fields (FP64 data, FP32-pipe arithmetic, about 48-bit significands), so the
-    // residual, its FP32 rounding for the inner solve and its norm come from one
-    // pass, and the solution update needs no FP64 arithmetic.  FP64 inner solves
-    // keep the outer loop in FP64.
-    const bool df = P != QXD_FP64;
+    // Mixed inner precision: the outer loop holds x and D x as double-float fields
+    // (FP64 data, FP32-pipe arithmetic, about 48-bit significands; eta is split on the
+    // fly), so the residual, its FP32 rounding for the inner solve and its norm come
+    // from one pass, and the solution update needs no FP64 arithmetic.  FP64 inner
+    // solves keep the outer loop in FP64, and so does a lattice whose double-float
+    // copies of the links and site-diagonal terms do not fit in the device memory.
+    bool df = P != QXD_FP64;
+    if (df && ensure_df64(ctx, fl, st) != QXD_OK) df = false;
     const size_t hb64 = half_bytes(ctx, QXD_FP64);
     const size_t hbP = half_bytes(ctx, Pv);
     void *re, *ro, *t64, *bP, *roP, *tP, *eeP, *eoP, *to2;
@@ -392,18 +394,16 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 17, hbP, &eoP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 18, hbP, &to2));
     Full r{re, ro};
-    void *xde = nullptr, *xdo = nullptr, *ede = nullptr, *edo = nullptr, *dxe = nullptr, *dxo = nullptr;
+    void *xde = nullptr, *xdo = nullptr, *dxe = nullptr, *dxo = nullptr;
     if (df) {
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 30, hb64, &xde));
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 31, hb64, &xdo));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 32, hb64, &ede));
-        QXD_TRY(qxd_ws(ctx, WS_SOLVER + 33, hb64, &edo));
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 34, hb64, &dxe));
         QXD_TRY(qxd_ws(ctx, WS_SOLVER + 35, hb64, &dxo));
     }
-    if (df) {  // the source's double-float copy and its norm in one pass per half
-        QXD_TRY(blas_split_df64_norm(ctx, eta.e, ede, n, 0, st));
-        QXD_TRY(blas_split_df64_norm(ctx, eta.o, edo, n, 2, st));
+    if (df) {  // the source's FP32 rounding for the first inner solve and its norm, one pass per half
+        QXD_TRY(blas_f64_to_f32_norm(ctx, eta.e, tP, 0, st));
+        QXD_TRY(blas_f64_to_f32_norm(ctx, eta.o, roP, 2, st));
     } else {
         QXD_TRY(blas_norm2(ctx, 0, n, eta.e, 0, st));
         QXD_TRY(blas_norm2(ctx, 0, n, eta.o, 2, st));
@@ -424,8 +424,6 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
     if (df) {
         QXD_CUDA(ctx, cudaMemsetAsync(xde, 0, hb64, st));
         QXD_CUDA(ctx, cudaMemsetAsync(xdo, 0, hb64, st));
-        QXD_TRY(blas_df_to_f32(ctx, ede, tP, st));
-        QXD_TRY(blas_df_to_f32(ctx, edo, roP, st));
     } else {
         QXD_CUDA(ctx, cudaMemcpyAsync(r.e, eta.e, hb64, cudaMemcpyDeviceToDevice, st));
         QXD_CUDA(ctx, cudaMemcpyAsync(r.o, eta.o, hb64, cudaMemcpyDeviceToDevice, st));
@@ -436,8 +434,8 @@ int solve_fgcr_dc(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full& eta, co
         double rr;
         if (df) {
             QXD_TRY(op_Dw(ctx, fl, QXD_DF64, Full{xde, xdo}, Full{dxe, dxo}, st));
-            QXD_TRY(blas_df_residual(ctx, ede, dxe, tP, 0, st));
-            QXD_TRY(blas_df_residual(ctx, edo, dxo, roP, 2, st));
+            QXD_TRY(blas_df_residual(ctx, eta.e, dxe, tP, 0, st));
+            QXD_TRY(blas_df_residual(ctx, eta.o, dxo, roP, 2, st));
             QXD_TRY(blas_fetch(ctx, 4, st));
             QXD_TRY(status_of_norm(ctx, ctx->red_host[1] + ctx->red_host[3], "residual"));
             rr = ctx->red_host[0] + ctx->red_host[2];
@@ -943,6 +941,24 @@ namespace qxd {
 // launch pair (links and site-diagonal terms read once).  Each right-hand side
 // has its own GCR scalars and stops independently (a finished one keeps its
 // solution and is no longer updated).
+// workspace of the batched inner solve: r, t_o, scratch, the two Krylov bases, one
+// preconditioner scratch field and the basis-precision copy of e
+struct BatchedWs {
+    void *rv, *tov, *tmpv, *Zv, *Wv, *ztmp, *tbv;
+};
+static int batched_inner_ws(qxd_ctx* ctx, int P, int nkv, int B, BatchedWs* w) {
+    const int Pb = P, Pv = vec_prec(P);
+    const size_t hb = half_bytes(ctx, Pb), hv = half_bytes(ctx, Pv);
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 130, hv * B, &w->rv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 131, hb * B, &w->tov));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 132, hb * B, &w->tmpv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 133, hb * B * nkv, &w->Zv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 134, hb * B * nkv, &w->Wv));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 135, hv, &w->ztmp));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 136, hb * B, &w->tbv));
+    return QXD_OK;
+}
+
 static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, const char* b, char* e, int B,
                               int max_iter, const std::vector<double>& rtol, std::vector<int>& iters, bool* stagnated,
                               cudaStream_t st) {
@@ -952,14 +968,9 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
     const bool split = Pb != Pv;
     const size_t n = 12ull * ctx->g.Vh;
     const size_t hb = half_bytes(ctx, Pb), hv = half_bytes(ctx, Pv);
-    void *rv, *tov, *tmpv, *Zv, *Wv, *ztmp, *tbv;
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 130, hv * B, &rv));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 131, hb * B, &tov));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 132, hb * B, &tmpv));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 133, hb * B * nkv, &Zv));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 134, hb * B * nkv, &Wv));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 135, hv, &ztmp));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 136, hb * B, &tbv));
+    BatchedWs w;
+    QXD_TRY(batched_inner_ws(ctx, P, nkv, B, &w));
+    void *rv = w.rv, *tov = w.tov, *tmpv = w.tmpv, *Zv = w.Zv, *Wv = w.Wv, *ztmp = w.ztmp, *tbv = w.tbv;
     char* r = static_cast<char*>(rv);
     char* Z = static_cast<char*>(Zv);
     char* W = static_cast<char*>(Wv);
@@ -994,29 +1005,37 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
         for (int j = 0; j < B; ++j) rr_cycle[j] = rr[j];
         std::vector<char> active(done.begin(), done.end());
         for (int j = 0; j < B; ++j) active[j] = !done[j];
+        // Without a preconditioner (and one basis precision) the direction of step k is
+        // the residual r_k itself, kept in Z_k; the fused step writes r_{k+1} into Z_{k+1}
+        // (into r after the last step of a cycle), as in fgcr_inner.
+        const bool rz = s->precond == QXD_PRECOND_NONE && !split;
+        if (rz) QXD_CUDA(ctx, cudaMemcpyAsync(Zk(0, 0), r, hb * B, cudaMemcpyDeviceToDevice, st));
         for (int k = 0; k < nkv; ++k) {
-            if (s->precond == QXD_PRECOND_NONE && !split) {
-                QXD_CUDA(ctx, cudaMemcpyAsync(Zk(k, 0), r, hb * B, cudaMemcpyDeviceToDevice, st));
-            } else if (s->precond == QXD_PRECOND_NONE) {
+            if (!rz && s->precond == QXD_PRECOND_NONE) {
                 QXD_TRY(blas_axpby(ctx, Pv, Pb, n * B, 1.0, 0.0, r, 0.0, 0.0, Zk(k, 0), st));
-            } else {
+            } else if (!rz) {
                 for (int j = 0; j < B; ++j)
                     if (active[j] == 1) QXD_TRY(precond_into(ctx, fl, Pv, Pb, s->precond, Rj(j), Zk(k, j), ztmp, st));
             }
             QXD_TRY(op_Dhat(ctx, fl, Pb, 0, Zk(k, 0), Wk(k, 0), tov, st, B));
+            // per right-hand side (nv complex slots each): <W_q, w> (q < k), <r, w> and,
+            // with rz, |w|^2
+            const int nv = k + 1 + (rz ? 1 : 0);
             for (int j = 0; j < B; ++j) {
                 if (active[j] != 1) continue;
                 for (int q = 0; q < k; ++q) Wc[q] = Wk(q, j);
-                int nd = k;
-                if (!split) Wc[nd++] = Rj(j);
-                if (nd > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, nd, Wc.data(), Wk(k, j), 2 * (k + 1) * j, st));
-                if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, Rj(j), Wk(k, j), 2 * (k + 1) * j + 2 * k, st));
+                int m = k;
+                if (!split) Wc[m++] = rz ? static_cast<const void*>(Zk(k, j)) : static_cast<const void*>(Rj(j));
+                if (rz) Wc[m++] = Wk(k, j);
+                if (m > 0) QXD_TRY(blas_multi_dot(ctx, Pb, n, m, Wc.data(), Wk(k, j), 2 * nv * j, st));
+                if (split) QXD_TRY(blas_dot(ctx, Pv, Pb, n, Rj(j), Wk(k, j), 2 * nv * j + 2 * k, st));
             }
-            QXD_TRY(blas_fetch(ctx, 2 * (k + 1) * B, st));
-            std::vector<double> wr_re(B), wr_im(B);
+            QXD_TRY(blas_fetch(ctx, 2 * nv * B, st));
+            std::vector<double> wr_re(B), wr_im(B), w2o(B, 0.0);
+            std::vector<char> fused(B, 0);
             for (int j = 0; j < B; ++j) {
                 if (active[j] != 1) continue;
-                const double* h = ctx->red_host + 2 * (k + 1) * j;
+                const double* h = ctx->red_host + 2 * nv * j;
                 for (int q = 0; q < k; ++q) {
                     const size_t o = ((size_t)j * nkv + q) * nkv + k;
                     Rre[o] = h[2 * q] / ww[(size_t)j * nkv + q];
@@ -1024,9 +1043,22 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
                 }
                 wr_re[j] = h[2 * k];
                 wr_im[j] = -h[2 * k + 1];
+                if (rz) {
+                    // |w'|^2 = |w|^2 - sum_q |<W_q, w>|^2 / |W_q|^2 unless it cancels below 1 %
+                    const double w2 = h[2 * (k + 1)];
+                    double v = w2;
+                    for (int q = 0; q < k; ++q)
+                        v -= (h[2 * q] * h[2 * q] + h[2 * q + 1] * h[2 * q + 1]) / ww[(size_t)j * nkv + q];
+                    if (std::isfinite(v) && v > 0.01 * w2) {
+                        fused[j] = 1;
+                        w2o[j] = v;
+                    }
+                }
             }
+            bool need_norm = false;
             for (int j = 0; j < B; ++j) {
-                if (active[j] != 1) continue;
+                if (active[j] != 1 || fused[j]) continue;
+                need_norm = true;
                 for (int q = 0; q < k; ++q) {
                     const size_t o = ((size_t)j * nkv + q) * nkv + k;
                     cre[q] = -Rre[o];
@@ -1035,17 +1067,38 @@ static int fgcr_inner_batched(qxd_ctx* ctx, int fl, int P, const qxd_solver* s, 
                 }
                 QXD_TRY(blas_multi_axpy_norm(ctx, Pb, n, k, cre.data(), cim.data(), Wc.data(), Wk(k, j), 2 * j, st));
             }
-            QXD_TRY(blas_fetch(ctx, 2 * B, st));
+            if (need_norm) QXD_TRY(blas_fetch(ctx, 2 * B, st));
             for (int j = 0; j < B; ++j) {
                 if (active[j] != 1) continue;
-                QXD_TRY(status_of_norm(ctx, ctx->red_host[2 * j + 1], "GCR"));
-                const double w2 = ctx->red_host[2 * j];
+                double w2;
+                if (fused[j]) {
+                    w2 = w2o[j];
+                } else {
+                    QXD_TRY(status_of_norm(ctx, ctx->red_host[2 * j + 1], "GCR"));
+                    w2 = ctx->red_host[2 * j];
+                }
                 if (!(w2 > 0.0)) return qxd_fail(ctx, QXD_EBREAKDOWN, "GCR: |w| = 0");
                 ww[(size_t)j * nkv + k] = w2;
-                are[(size_t)j * nkv + k] = wr_re[j] / w2;
-                aim[(size_t)j * nkv + k] = wr_im[j] / w2;
-                QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -are[(size_t)j * nkv + k], -aim[(size_t)j * nkv + k], Wk(k, j), 1.0,
-                                   0.0, Rj(j), st));
+                const double ar = wr_re[j] / w2, ai = wr_im[j] / w2;
+                are[(size_t)j * nkv + k] = ar;
+                aim[(size_t)j * nkv + k] = ai;
+                if (rz) {
+                    void* next = k + 1 < nkv ? static_cast<void*>(Zk(k + 1, j)) : static_cast<void*>(Rj(j));
+                    if (fused[j]) {
+                        for (int q = 0; q < k; ++q) {
+                            const size_t o = ((size_t)j * nkv + q) * nkv + k;
+                            cre[q] = -Rre[o];
+                            cim[q] = -Rim[o];
+                            Wc[q] = Wk(q, j);
+                        }
+                        QXD_TRY(blas_gcr_update(ctx, Pb, n, k, cre.data(), cim.data(), Wc.data(), Wk(k, j), -ar, -ai,
+                                                Zk(k, j), next, st));
+                    } else {
+                        QXD_TRY(blas_axpy3(ctx, Pb, n, -ar, -ai, Wk(k, j), Zk(k, j), next, st));
+                    }
+                } else {
+                    QXD_TRY(blas_axpby(ctx, Pb, Pv, n, -ar, -ai, Wk(k, j), 1.0, 0.0, Rj(j), st));
+                }
                 rr[j] -= (wr_re[j] * wr_re[j] + wr_im[j] * wr_im[j]) / w2;
                 iters[j] += 1;
             }
@@ -1118,21 +1171,48 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
     const size_t n = 12ull * ctx->g.Vh;
     const int P = s->inner;
     const int Pv = vec_prec(P);
+    // as in solve_fgcr_dc: with FP32/BF16 inner solves the outer loop holds x and D x as
+    // double-float fields (one multi-right-hand-side double-float D_w per outer step);
+    // FP64 inner solves keep it in FP64, and so does a lattice whose double-float copies
+    // of the links and site-diagonal terms do not fit in the device memory
+    bool df = P != QXD_FP64;
     const size_t hb64 = half_bytes(ctx, QXD_FP64), hbP = half_bytes(ctx, Pv);
-    void *re, *ro, *bP, *roP, *tP, *eeP, *eoP, *to2;
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 140, hb64 * B, &re));
-    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 141, hb64 * B, &ro));
+    // the FP64-sized pair holds x (double-float) or the residual r (FP64 outer loop)
+    void *s0, *s1, *bP, *roP, *tP, *eeP, *eoP, *to2;
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 140, hb64 * B, &s0));
+    QXD_TRY(qxd_ws(ctx, WS_SOLVER + 141, hb64 * B, &s1));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 142, hbP * B, &bP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 143, hbP * B, &roP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 144, hbP * B, &tP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 145, hbP * B, &eeP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 146, hbP * B, &eoP));
     QXD_TRY(qxd_ws(ctx, WS_SOLVER + 147, hbP * B, &to2));
+    if (df) {
+        // the inner solve's workspace first, so that the copies take only what is left
+        BatchedWs w;
+        QXD_TRY(batched_inner_ws(ctx, P, nkv, B, &w));
+        if (ensure_df64(ctx, fl, st) != QXD_OK) df = false;
+    }
+    void *re = nullptr, *ro = nullptr, *xde = nullptr, *xdo = nullptr;
+    if (df) {
+        xde = s0;
+        xdo = s1;
+    } else {
+        re = s0;
+        ro = s1;
+    }
     char* E = static_cast<char*>(eeP);
+    auto at = [](void* base, size_t stride, int j) { return static_cast<char*>(base) + (size_t)j * stride; };
+    auto cat = [](const void* base, size_t stride, int j) { return static_cast<const char*>(base) + (size_t)j * stride; };
     std::vector<double> enorm(B), relres(B, 1.0);
     for (int j = 0; j < B; ++j) {
-        QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(eta.e) + j * hb64, 4 * j, st));
-        QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(eta.o) + j * hb64, 4 * j + 2, st));
+        if (df) {  // the sources' FP32 roundings for the first inner solve and their norms
+            QXD_TRY(blas_f64_to_f32_norm(ctx, cat(eta.e, hb64, j), at(tP, hbP, j), 4 * j, st));
+            QXD_TRY(blas_f64_to_f32_norm(ctx, cat(eta.o, hb64, j), at(roP, hbP, j), 4 * j + 2, st));
+        } else {
+            QXD_TRY(blas_norm2(ctx, 0, n, cat(eta.e, hb64, j), 4 * j, st));
+            QXD_TRY(blas_norm2(ctx, 0, n, cat(eta.o, hb64, j), 4 * j + 2, st));
+        }
     }
     QXD_TRY(blas_fetch(ctx, 4 * B, st));
     for (int j = 0; j < B; ++j) {
@@ -1141,8 +1221,54 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
     }
     QXD_CUDA(ctx, cudaMemsetAsync(x.e, 0, hb64 * B, st));
     QXD_CUDA(ctx, cudaMemsetAsync(x.o, 0, hb64 * B, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(re, eta.e, hb64 * B, cudaMemcpyDeviceToDevice, st));
-    QXD_CUDA(ctx, cudaMemcpyAsync(ro, eta.o, hb64 * B, cudaMemcpyDeviceToDevice, st));
+    if (df) {
+        QXD_CUDA(ctx, cudaMemsetAsync(xde, 0, hb64 * B, st));
+        QXD_CUDA(ctx, cudaMemsetAsync(xdo, 0, hb64 * B, st));
+    } else {
+        QXD_CUDA(ctx, cudaMemcpyAsync(re, eta.e, hb64 * B, cudaMemcpyDeviceToDevice, st));
+        QXD_CUDA(ctx, cudaMemcpyAsync(ro, eta.o, hb64 * B, cudaMemcpyDeviceToDevice, st));
+    }
+    // true residuals of the current x: relres[j]; in the double-float loop they also
+    // leave FP32(eta - D x) in tP, roP for the next inner solve
+    auto residuals = [&](bool* all) -> int {
+        if (df) {
+            // D x goes to the inner solver's Krylov-basis slot, which is free between inner solves
+            void* dx;
+            QXD_TRY(qxd_ws(ctx, WS_SOLVER + 133, 2 * hb64 * B, &dx));
+            char* dxe = static_cast<char*>(dx);
+            char* dxo = dxe + hb64 * B;
+            QXD_TRY(op_Dw(ctx, fl, QXD_DF64, Full{xde, xdo}, Full{dxe, dxo}, st, B));
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(blas_df_residual(ctx, cat(eta.e, hb64, j), at(dxe, hb64, j), at(tP, hbP, j), 4 * j, st));
+                QXD_TRY(blas_df_residual(ctx, cat(eta.o, hb64, j), at(dxo, hb64, j), at(roP, hbP, j), 4 * j + 2, st));
+            }
+        } else {
+            QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, Full{re, ro}, st, B));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.e, -1.0, 0.0, re, st));
+            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.o, -1.0, 0.0, ro, st));
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(blas_norm2(ctx, 0, n, at(re, hb64, j), 4 * j, st));
+                QXD_TRY(blas_norm2(ctx, 0, n, at(ro, hb64, j), 4 * j + 2, st));
+            }
+        }
+        QXD_TRY(blas_fetch(ctx, 4 * B, st));
+        *all = true;
+        for (int j = 0; j < B; ++j) {
+            QXD_TRY(status_of_norm(ctx, ctx->red_host[4 * j + 1] + ctx->red_host[4 * j + 3], "residual"));
+            relres[j] = enorm[j] > 0 ? std::sqrt(ctx->red_host[4 * j] + ctx->red_host[4 * j + 2]) / enorm[j] : 0.0;
+            *all = *all && relres[j] <= s->tol;
+        }
+        return QXD_OK;
+    };
+    // the double-float solutions go to the caller's FP64 fields
+    auto finish = [&]() -> int {
+        if (df)
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(blas_join_df64(ctx, at(xde, hb64, j), at(x.e, hb64, j), n, st));
+                QXD_TRY(blas_join_df64(ctx, at(xdo, hb64, j), at(x.o, hb64, j), n, st));
+            }
+        return QXD_OK;
+    };
     const double itol = s->inner_tol > 0 ? s->inner_tol : (P == QXD_BF16 ? 5e-3 : (P == QXD_FP32 ? 1e-5 : 1e-10));
     info->iters = 0;
     info->restarts = 0;
@@ -1151,21 +1277,8 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
     bool use_cgnr = false;
     for (int outer = 0; outer < 64; ++outer) {
         if (outer > 0) {
-            // r = eta - D x for the whole batch (FP64)
-            QXD_TRY(op_Dw(ctx, fl, QXD_FP64, x, Full{re, ro}, st, B));
-            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.e, -1.0, 0.0, re, st));
-            QXD_TRY(blas_axpby(ctx, 0, 0, n * B, 1.0, 0.0, eta.o, -1.0, 0.0, ro, st));
-            for (int j = 0; j < B; ++j) {
-                QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(re) + j * hb64, 4 * j, st));
-                QXD_TRY(blas_norm2(ctx, 0, n, static_cast<char*>(ro) + j * hb64, 4 * j + 2, st));
-            }
-            QXD_TRY(blas_fetch(ctx, 4 * B, st));
-            bool all = true;
-            for (int j = 0; j < B; ++j) {
-                QXD_TRY(status_of_norm(ctx, ctx->red_host[4 * j + 1] + ctx->red_host[4 * j + 3], "residual"));
-                relres[j] = enorm[j] > 0 ? std::sqrt(ctx->red_host[4 * j] + ctx->red_host[4 * j + 2]) / enorm[j] : 0.0;
-                all = all && relres[j] <= s->tol;
-            }
+            bool all = false;
+            QXD_TRY(residuals(&all));
             info->op_applies += B;
             if (verbose()) std::fprintf(stderr, "[qxd dc-batched] outer %d worst relres %.3e\n", outer,
                                         *std::max_element(relres.begin(), relres.end()));
@@ -1173,8 +1286,10 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
             info->restarts += 1;
         }
         if (info->iters >= s->nmx) break;
-        QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, re, 0.0, 0.0, tP, st));
-        QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, ro, 0.0, 0.0, roP, st));
+        if (!df) {
+            QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, re, 0.0, 0.0, tP, st));
+            QXD_TRY(blas_axpby(ctx, 0, Pv, n * B, 1.0, 0.0, ro, 0.0, 0.0, roP, st));
+        }
         QXD_TRY(op_eo_source(ctx, fl, Pv, Full{tP, roP}, bP, to2, st, B));
         std::vector<double> rtol(B);
         for (int j = 0; j < B; ++j) rtol[j] = relres[j] <= s->tol ? 1.0 : std::max(itol, 0.5 * s->tol / relres[j]);
@@ -1207,9 +1322,17 @@ int solve_fgcr_dc_batched(qxd_ctx* ctx, int fl, const qxd_solver* s, const Full&
         info->iters += mx;
         info->op_applies += mx * B;
         QXD_TRY(op_odd_reconstruct(ctx, fl, Pv, roP, E, eoP, st, B));
-        QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, E, 1.0, 0.0, x.e, st));
-        QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        if (df) {
+            for (int j = 0; j < B; ++j) {
+                QXD_TRY(blas_df_add_f32(ctx, at(eeP, hbP, j), at(xde, hb64, j), st));
+                QXD_TRY(blas_df_add_f32(ctx, at(eoP, hbP, j), at(xdo, hb64, j), st));
+            }
+        } else {
+            QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, E, 1.0, 0.0, x.e, st));
+            QXD_TRY(blas_axpby(ctx, Pv, 0, n * B, 1.0, 0.0, eoP, 1.0, 0.0, x.o, st));
+        }
     }
+    QXD_TRY(finish());
     double worst = 0.0;
     for (int j = 0; j < B; ++j) worst = std::max(worst, relres[j]);
     info->true_relres = worst;

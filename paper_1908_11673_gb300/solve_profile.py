@@ -45,6 +45,7 @@ def main(argv=None):
     ap.add_argument("--nmr", type=int, default=5)
     ap.add_argument("--nkv", type=int, default=16)
     ap.add_argument("--inner", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides solved in lockstep (FGCR)")
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--top", type=int, default=10)
     args = ap.parse_args(argv)
@@ -56,7 +57,10 @@ def main(argv=None):
     ctx = qxd.Context(L, args.cstar, (np.pi, 0.0, 0.0, 0.0))
     ctx.set_links(U, A, 6.0)
     ctx.set_clover(0, args.qhat, args.kappa, 1.90952, 1.0)
-    eta = torch.from_numpy(workload.spinor(ctx.V, args.seed + 1)).cuda()
+    if args.nrhs == 1:
+        eta = torch.from_numpy(workload.spinor(ctx.V, args.seed + 1)).cuda()
+    else:
+        eta = torch.from_numpy(np.stack([workload.spinor(ctx.V, args.seed + 1 + j) for j in range(args.nrhs)])).cuda()
     psi = torch.empty_like(eta)
     ctx.set_sap(args.ncy, args.nmr)
     kind = qxd.FGCR if args.solver == "fgcr" else qxd.CGNE
@@ -76,7 +80,7 @@ def main(argv=None):
         ctx.profile(2)
         torch.cuda.synchronize()
         t = time.perf_counter()
-        info = ctx.solve(0, eta, psi, kind=kind, tol=1e-10, inner=inner, nkv=args.nkv, precond=pre)
+        info = ctx.solve(0, eta, psi, kind=kind, tol=1e-10, inner=inner, nkv=args.nkv, precond=pre, nrhs=args.nrhs)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t
         prof = ctx.profile_entries()

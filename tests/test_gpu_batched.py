@@ -65,46 +65,48 @@ def test_config5_48c96_two_flavours_bf16_batched():
     U, A0 = workload.gauge_field(L, 5000, stout_steps=5, device="cuda")
     torch.cuda.empty_cache()
     ctx = qxd.Context(L, 3, (np.pi, 0, 0, 0))
-    ctx.set_links(U, A0, 6.0)
-    assert ctx.V == 21233664
-    ctx.set_clover(0, 4, 0.137312, 1.90952, 1.90952)
-    ld0, nneg0 = ctx.sdet(0)
-    A = workload.u1_stout(A0, L, 5, 0.1, device="cuda")
-    del A0
-    ctx.set_links(U, A, 6.0)
-    ctx.set_clover(0, 4, 0.137312, 1.90952, 1.90952)
-    ld1, nneg1 = ctx.sdet(0)
-    print(f"config5 qhat=4 odd sites with det D_oo < 0: unsmeared photon field {nneg0}, smeared {nneg1}; "
-          f"sum log|det D_oo| {ld0:.6e} / {ld1:.6e}", flush=True)
-    geom = Geometry(L, 3, (np.pi, 0, 0, 0))
-    gauge = GaugeField(geom, U, A, 6.0)
-    rng = np.random.default_rng(5)
-    for qhat, kappa in [(4, 0.137312), (-2, 0.136377)]:
-        ctx.set_clover(0, qhat, kappa, 1.90952, 1.90952)
-        op = DiracOperator(gauge, Flavour(qhat, kappa, 1.90952, 1.90952))
-        sites = rng.choice(ctx.V, 400, replace=False)
-        eta = torch.from_numpy(workload.spinor(ctx.V, 5001, nrhs=4)).cuda()
-        out = torch.empty_like(eta)
-        ctx.apply_Dw(0, 0, eta, out, nrhs=4)
-        for r in range(4):
-            ref = op.apply(eta[r].cpu().numpy(), sites)
-            assert relerr(out[r].cpu().numpy()[sites], ref) <= 1e-13
-        e32 = eta.to(torch.complex64)
-        o32 = torch.empty_like(e32)
-        ctx.apply_Dw(0, 2, e32, o32, nrhs=4)
-        for r in range(4):
-            ref = op.apply(e32[r].cpu().numpy().astype(np.complex128), sites)
-            assert relerr(o32[r].cpu().numpy()[sites].astype(np.complex128), ref) <= BF16_TOL
-        del out, e32, o32
-        psi = torch.empty_like(eta)
-        t1 = time.time()
-        info = ctx.solve(0, eta, psi, kind=1, tol=1e-10, inner=2, nkv=8, nrhs=4)
-        torch.cuda.synchronize()
-        print(f"config5 qhat={qhat}: {info.asdict()} solve {time.time() - t1:.1f} s at {time.time() - t0:.1f} s",
-              flush=True)
-        assert info.status == 0 and info.true_relres <= 1e-10, info.asdict()
-        sites = rng.choice(ctx.V, 800, replace=False)
-        res = oracle_residuals(op, eta.cpu().numpy(), psi.cpu().numpy(), sites)
-        assert max(res) < 1e-9, res
-        del psi, eta
-    ctx.close()
+    try:
+        ctx.set_links(U, A0, 6.0)
+        assert ctx.V == 21233664
+        ctx.set_clover(0, 4, 0.137312, 1.90952, 1.90952)
+        ld0, nneg0 = ctx.sdet(0)
+        A = workload.u1_stout(A0, L, 5, 0.1, device="cuda")
+        del A0
+        ctx.set_links(U, A, 6.0)
+        ctx.set_clover(0, 4, 0.137312, 1.90952, 1.90952)
+        ld1, nneg1 = ctx.sdet(0)
+        print(f"config5 qhat=4 odd sites with det D_oo < 0: unsmeared photon field {nneg0}, smeared {nneg1}; "
+              f"sum log|det D_oo| {ld0:.6e} / {ld1:.6e}", flush=True)
+        geom = Geometry(L, 3, (np.pi, 0, 0, 0))
+        gauge = GaugeField(geom, U, A, 6.0)
+        rng = np.random.default_rng(5)
+        for qhat, kappa in [(4, 0.137312), (-2, 0.136377)]:
+            ctx.set_clover(0, qhat, kappa, 1.90952, 1.90952)
+            op = DiracOperator(gauge, Flavour(qhat, kappa, 1.90952, 1.90952))
+            sites = rng.choice(ctx.V, 400, replace=False)
+            eta = torch.from_numpy(workload.spinor(ctx.V, 5001, nrhs=4)).cuda()
+            out = torch.empty_like(eta)
+            ctx.apply_Dw(0, 0, eta, out, nrhs=4)
+            for r in range(4):
+                ref = op.apply(eta[r].cpu().numpy(), sites)
+                assert relerr(out[r].cpu().numpy()[sites], ref) <= 1e-13
+            e32 = eta.to(torch.complex64)
+            o32 = torch.empty_like(e32)
+            ctx.apply_Dw(0, 2, e32, o32, nrhs=4)
+            for r in range(4):
+                ref = op.apply(e32[r].cpu().numpy().astype(np.complex128), sites)
+                assert relerr(o32[r].cpu().numpy()[sites].astype(np.complex128), ref) <= BF16_TOL
+            del out, e32, o32
+            psi = torch.empty_like(eta)
+            t1 = time.time()
+            info = ctx.solve(0, eta, psi, kind=1, tol=1e-10, inner=2, nkv=8, nrhs=4)
+            torch.cuda.synchronize()
+            print(f"config5 qhat={qhat}: {info.asdict()} solve {time.time() - t1:.1f} s at {time.time() - t0:.1f} s",
+                  flush=True)
+            assert info.status == 0 and info.true_relres <= 1e-10, info.asdict()
+            sites = rng.choice(ctx.V, 800, replace=False)
+            res = oracle_residuals(op, eta.cpu().numpy(), psi.cpu().numpy(), sites)
+            assert max(res) < 1e-9, res
+            del psi, eta
+    finally:
+        ctx.close()  # also when an assertion fails: the context holds most of the device memory
