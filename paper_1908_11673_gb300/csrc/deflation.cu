@@ -8,13 +8,14 @@
 //   A          little Dirac operator P^+ D P: per block B, nine Ns x Ns blocks
 //              (B itself and the blocks across its eight faces)
 //   M_dfl v  = P A^-1 P^+ v + M_sap (v - D P A^-1 P^+ v), with A^-1 from restarted
-//              GCR on the block grid to a relative residual ctol
+//              GCR on the block grid to a relative residual ctol (one cooperative
+//              launch, k_dfl_gcr)
 //
 // Layout.  The basis is Ns full FP32 fields in the internal layout (even half,
 // odd half).  Coarse vectors are complex FP32 arrays [Nb][Ns].  A is stored as
 // A[B][s][l][k] = <phi_k|_B, D phi_l|_{B_s}> (s = 0 the block itself, 1 + 2 mu the
-// block across the +mu face, 2 + 2 mu across the -mu face), so that lane k of a
-// warp reads consecutive entries when it forms row k of A x.
+// block across the +mu face, 2 + 2 mu across the -mu face), so that the lanes that
+// form rows k = 0 .. Ns-1 of A x read consecutive entries.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
